@@ -1,0 +1,144 @@
+/*
+ * ilg.h — C ABI of libilg.so, the GB300 (sm_103a) implementation of the
+ * over-relaxed diffusive integer lattice gas of Strand & Wagner,
+ * "Over-Relaxation in Diffusive Integer Lattice Gas" (arXiv 2203.01380).
+ *
+ * One time step, for every node x of a periodic D1Q3 or D2Q5 lattice:
+ *   flip      m_i = n_{-i}(x,t) when omega_eff > 1            (Sec. III, Eq. flip)
+ *   collide   sampling collision with fraction omega*:         (Sec. II; Sec. III, Eq. LGflip)
+ *             binomial thinning, multinomial redistribution
+ *             with weights w_i; mass conserved exactly         (Sec. II, Eq. 2)
+ *   stream    n_i(x + v_i, t+1) = n'_i(x)                      (Sec. II, Eq. ilgeq)
+ * with omega^j = 2 - omega* above omega_eff = 1                 (Sec. IV, Eq. omegaj).
+ *
+ * Conventions
+ *   - Occupations are uint16, stored as Q planes n[i][y][x] (x fastest), velocity
+ *     order rest first: D1Q3 (0, +1, -1); D2Q5 (0, +x, -x, +y, -y), y = row.
+ *   - The library owns the device memory of a context; the caller owns every host
+ *     array it passes and keeps it alive for the duration of the call.
+ *   - Calls on one context are not thread-safe; different contexts are independent.
+ *   - Every call returns an ilg_status; no C++ exception crosses the ABI.
+ *     ilg_last_error() describes the last failure on a context.
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream).  Kernels of a
+ *     context run on its stream; calls that return host data synchronise it.
+ *   - Random numbers: Philox4x32-10, key = seed, counter = (node x + Lx*y, step t,
+ *     replica, purpose tag and block).  Results do not depend on launch shape,
+ *     stream, batching or placement.
+ */
+#ifndef ILG_H
+#define ILG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ILG_OK = 0,
+  ILG_E_INVALID = 1,  /* bad argument or parameter */
+  ILG_E_OOM = 2,      /* device allocation failed */
+  ILG_E_OVERFLOW = 3, /* some occupation would exceed 65535; state rolled back */
+  ILG_E_CUDA = 4,     /* CUDA runtime error */
+  ILG_E_TIMEOUT = 5,  /* a bounded device wait gave up */
+  ILG_E_STATE = 6     /* call out of order (e.g. step before init/set_state) */
+} ilg_status;
+
+typedef enum { ILG_D1Q3 = 1, ILG_D2Q5 = 2 } ilg_lattice;
+
+/* Parameters of one lattice (Sec. II-V).
+ *   lattice        ILG_D1Q3 or ILG_D2Q5
+ *   Lx, Ly         periodic extent, >= 3 each (Ly is ignored and taken as 1 for D1Q3);
+ *                  Lx * Ly < 2^32
+ *   n0, amp        initial state (Sec. V): see init_weighted
+ *   mode_mx/my     wave numbers of the initial sine, k = 2 pi (mx/Lx, my/Ly); at most
+ *                  one of them nonzero (an axis mode)
+ *   init_weighted  1: mean of velocity i is w_i (Q n0 + amp sin(k.x))  (Sec. V, w_i P(rho));
+ *                  0: mean of every velocity is n0 + amp sin(k.x) / Q
+ *                  every mean must lie in [0, 700]
+ *   omega_eff      in (0, 2]: <= 1 collision fraction omega* = omega_eff without flip;
+ *                  > 1 flip on and omega* = 2 - omega_eff, so omega^j = omega_eff
+ *   theta          D1Q3 weights (1-theta, theta/2, theta/2), theta in (0, 1);
+ *                  D2Q5 weights (1-2 theta, theta/2 x4), theta in (0, 1/2]
+ *   seed, replica  Philox key and the replica word of every counter */
+typedef struct {
+  int32_t lattice;
+  uint32_t Lx;
+  uint32_t Ly;
+  int32_t mode_mx;
+  int32_t mode_my;
+  int32_t init_weighted;
+  double n0;
+  double amp;
+  double omega_eff;
+  double theta;
+  uint64_t seed;
+  uint32_t replica;
+  uint32_t reserved; /* must be 0 */
+} ilg_params;
+
+typedef struct ilg_ctx ilg_ctx;
+
+/* Create a context for one lattice: validates params, allocates two state buffers
+ * (2 * Q * Lx * Ly uint16) plus tables and reduction scratch on the current device,
+ * and builds the integer CDF tables of the collision.  *out is NULL on failure. */
+ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out);
+
+/* Release every device allocation of the context (after synchronising its stream). */
+ilg_status ilg_destroy(ilg_ctx* ctx);
+
+/* Message describing the last failure on ctx (empty string if none); valid until
+ * the next call on ctx.  ilg_last_error(NULL) describes the last failed ilg_create. */
+const char* ilg_last_error(const ilg_ctx* ctx);
+
+/* Poisson initial state of Sec. V (means as in ilg_params), step counter t := 0.
+ * ILG_E_INVALID if a mean lies outside [0, 700]. */
+ilg_status ilg_init(ilg_ctx* ctx);
+
+/* Copy a state in: host (pageable or pinned) or device array of n = Q*Lx*Ly uint16 in
+ * the plane layout above, at step t (t < 2^32).  Synchronous. */
+ilg_status ilg_set_state(ilg_ctx* ctx, const uint16_t* host, size_t n, uint64_t t);
+ilg_status ilg_set_state_device(ilg_ctx* ctx, const uint16_t* dev, size_t n, uint64_t t);
+
+/* Copy the current state out (n = Q*Lx*Ly) and its step counter (t may be NULL).
+ * Synchronous. */
+ilg_status ilg_get_state(ilg_ctx* ctx, uint16_t* host, size_t n, uint64_t* t);
+ilg_status ilg_get_state_device(ilg_ctx* ctx, uint16_t* dev, size_t n, uint64_t* t);
+
+/* Advance T time steps (t -> t + T; t + T must stay below 2^32).  Kernels are queued
+ * on the context stream; the call then reads one overflow word back (synchronising
+ * the stream).  On ILG_E_OVERFLOW the context holds the state and step counter of
+ * the last completed step before the failing one. */
+ilg_status ilg_step(ilg_ctx* ctx, uint32_t T);
+
+/* Observables of the current state (Sec. V).  modes: nmodes pairs (mx, my), each an
+ * axis mode (one of the two zero, not both).  For a mode along x with
+ * D(x) = Lx*C(x) - M, C(x) = sum_y N(x,y), r = (mx*x) mod Lx:
+ *   re = sum_x cos(2 pi r / Lx) D(x) / Lx,  im = sum_x sin(2 pi r / Lx) D(x) / Lx,
+ *   amp = im / (Lx*Ly/2)  (A^LG of Sec. V),  Sk = (re^2 + im^2) / (Lx*Ly);
+ * modes along y use row sums R(y) and Ly.  Integer sums are exact (int64); the
+ * projections are compensated double-precision dot products.  Every output pointer
+ * is a host array (nmodes entries for re/im/amp/Sk, Lx for col_sums, Ly for
+ * row_sums) and may be NULL.  Synchronous. */
+ilg_status ilg_observables(ilg_ctx* ctx, const int32_t* modes, uint32_t nmodes, uint64_t* t,
+                           uint64_t* mass, double* re, double* im, double* amp, double* Sk,
+                           int64_t* col_sums, int64_t* row_sums);
+
+/* Diagnostics of the building blocks, for parity tests.
+ * ilg_philox: n Philox4x32-10 blocks computed on the device; ctr (4n words) and out
+ *   (4n words) are host arrays; key = (seed lo32, seed hi32).
+ * ilg_binomial_table: the 2080-entry integer CDF table (rows n = 1..64, row n at
+ *   offset n(n-1)/2) the collision uses for probability P / 2^32, 0 < P < 2^32; host
+ *   only, no device work.
+ * ilg_poisson_table: the Poisson CDF table of the initial state for mean lambda;
+ *   writes at most cap entries and their count to *K; host only. */
+ilg_status ilg_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t n, void* stream);
+ilg_status ilg_binomial_table(uint64_t P, uint32_t* out);
+ilg_status ilg_poisson_table(double lambda, uint32_t* out, uint32_t cap, uint32_t* K);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ILG_H */

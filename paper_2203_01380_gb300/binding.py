@@ -1,0 +1,196 @@
+"""ctypes binding of libilg.so (argument marshalling only; every step runs in the
+library's CUDA kernels).  Importing this module fails loudly when the library
+has not been built: there is no CPU fallback.
+
+Names follow ``include/ilg.h``; see that header for the meaning of every
+argument, the layouts and the error behaviour.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libilg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()'). "
+        "The lattice-gas path has no CPU fallback.")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+ILG_OK, ILG_E_INVALID, ILG_E_OOM, ILG_E_OVERFLOW, ILG_E_CUDA, ILG_E_TIMEOUT, ILG_E_STATE = range(7)
+D1Q3, D2Q5 = 1, 2
+STATUS_NAMES = {0: "ILG_OK", 1: "ILG_E_INVALID", 2: "ILG_E_OOM", 3: "ILG_E_OVERFLOW", 4: "ILG_E_CUDA",
+                5: "ILG_E_TIMEOUT", 6: "ILG_E_STATE"}
+
+
+class IlgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32), ("Lx", ctypes.c_uint32), ("Ly", ctypes.c_uint32),
+        ("mode_mx", ctypes.c_int32), ("mode_my", ctypes.c_int32), ("init_weighted", ctypes.c_int32),
+        ("n0", ctypes.c_double), ("amp", ctypes.c_double), ("omega_eff", ctypes.c_double),
+        ("theta", ctypes.c_double), ("seed", ctypes.c_uint64), ("replica", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+
+_vp = ctypes.c_void_p
+_u16p = np.ctypeslib.ndpointer(np.uint16, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+
+_lib.ilg_last_error.argtypes = [_vp]
+_lib.ilg_last_error.restype = ctypes.c_char_p
+_lib.ilg_create.argtypes = [ctypes.POINTER(Params), _vp, ctypes.POINTER(_vp)]
+_lib.ilg_destroy.argtypes = [_vp]
+_lib.ilg_init.argtypes = [_vp]
+_lib.ilg_set_state.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_uint64]
+_lib.ilg_set_state_device.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_uint64]
+_lib.ilg_get_state.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
+_lib.ilg_get_state_device.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
+_lib.ilg_step.argtypes = [_vp, ctypes.c_uint32]
+_lib.ilg_observables.argtypes = [_vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(ctypes.c_uint64), _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.ilg_philox.argtypes = [_u32p, ctypes.c_uint64, _u32p, ctypes.c_size_t, _vp]
+_lib.ilg_binomial_table.argtypes = [ctypes.c_uint64, _u32p]
+_lib.ilg_poisson_table.argtypes = [ctypes.c_double, _u32p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+for _f in ("ilg_create", "ilg_destroy", "ilg_init", "ilg_set_state", "ilg_set_state_device", "ilg_get_state",
+           "ilg_get_state_device", "ilg_step", "ilg_observables", "ilg_philox", "ilg_binomial_table",
+           "ilg_poisson_table"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+def lib():
+    return _lib
+
+
+def stream_handle(stream) -> int:
+    """cudaStream_t as an integer: None/0 -> legacy default stream; objects with
+    a ``cuda_stream`` attribute (e.g. torch.cuda.Stream) give theirs."""
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def _check(status: int, ctx=None):
+    if status != ILG_OK:
+        msg = _lib.ilg_last_error(ctx).decode(errors="replace")
+        raise IlgError(status, msg)
+
+
+def make_params(lattice, Lx, Ly=1, n0=10.0, amp=0.0, mode_mx=0, mode_my=0, init_weighted=0,
+                omega_eff=1.0, theta=1.0 / 3.0, seed=0, replica=0, **_ignored) -> Params:
+    return Params(int(lattice), int(Lx), int(Ly if lattice == D2Q5 else 1), int(mode_mx), int(mode_my),
+                  int(init_weighted), float(n0), float(amp), float(omega_eff), float(theta), int(seed),
+                  int(replica), 0)
+
+
+class Lattice:
+    """One lattice context (ilg_create ... ilg_destroy)."""
+
+    def __init__(self, lattice, Lx, Ly=1, stream=None, **kw):
+        self.params = make_params(lattice, Lx, Ly, **kw)
+        self.Q = 3 if lattice == D1Q3 else 5
+        self.Lx, self.Ly = self.params.Lx, self.params.Ly
+        self.stream = stream_handle(stream)
+        h = _vp()
+        _check(_lib.ilg_create(ctypes.byref(self.params), _vp(self.stream), ctypes.byref(h)), None)
+        self._h = h
+
+    @property
+    def shape(self):
+        return (self.Q, self.Ly, self.Lx)
+
+    @property
+    def size(self):
+        return self.Q * self.Ly * self.Lx
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ilg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init(self):
+        _check(_lib.ilg_init(self._h), self._h)
+
+    def set_state(self, state: np.ndarray, t: int = 0):
+        s = np.ascontiguousarray(state, dtype=np.uint16)
+        if s.size != self.size:
+            raise ValueError("state has the wrong size")
+        _check(_lib.ilg_set_state(self._h, s.ctypes.data, s.size, int(t)), self._h)
+
+    def set_state_device(self, ptr: int, n: int, t: int = 0):
+        _check(_lib.ilg_set_state_device(self._h, _vp(ptr), n, int(t)), self._h)
+
+    def get_state(self, out: np.ndarray | None = None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.uint16)
+        t = ctypes.c_uint64()
+        _check(_lib.ilg_get_state(self._h, out.ctypes.data, out.size, ctypes.byref(t)), self._h)
+        return out, int(t.value)
+
+    def get_state_device(self, ptr: int, n: int) -> int:
+        t = ctypes.c_uint64()
+        _check(_lib.ilg_get_state_device(self._h, _vp(ptr), n, ctypes.byref(t)), self._h)
+        return int(t.value)
+
+    def step(self, T: int):
+        _check(_lib.ilg_step(self._h, int(T)), self._h)
+
+    def observables(self, modes=(), col_sums=False, row_sums=False):
+        modes = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, 2))
+        n = len(modes)
+        re, im, amp, Sk = (np.zeros(n) for _ in range(4))
+        col = np.zeros(self.Lx, dtype=np.int64) if col_sums else None
+        row = np.zeros(self.Ly, dtype=np.int64) if row_sums else None
+        t = ctypes.c_uint64()
+        M = ctypes.c_uint64()
+        _check(_lib.ilg_observables(self._h, modes.ctypes.data if n else None, n, ctypes.byref(t), ctypes.byref(M),
+                                    re.ctypes.data, im.ctypes.data, amp.ctypes.data, Sk.ctypes.data,
+                                    col.ctypes.data if col is not None else None,
+                                    row.ctypes.data if row is not None else None), self._h)
+        return dict(t=int(t.value), mass=int(M.value), re=re, im=im, amp=amp, Sk=Sk, col=col, row=row)
+
+
+def philox(ctr: np.ndarray, seed: int, stream=None) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(ctr)
+    _check(_lib.ilg_philox(ctr.reshape(-1), int(seed), out.reshape(-1), len(ctr), _vp(stream_handle(stream))))
+    return out
+
+
+def binomial_table(P: int) -> np.ndarray:
+    out = np.zeros(2080, dtype=np.uint32)
+    _check(_lib.ilg_binomial_table(int(P), out))
+    return out
+
+
+def poisson_table(lam: float, cap: int = 4096) -> np.ndarray:
+    out = np.zeros(cap, dtype=np.uint32)
+    K = ctypes.c_uint32()
+    _check(_lib.ilg_poisson_table(float(lam), out, cap, ctypes.byref(K)))
+    return out[:K.value].copy()

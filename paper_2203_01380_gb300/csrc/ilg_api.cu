@@ -1,0 +1,407 @@
+// C ABI of libilg.so: contexts, validation, scheduling of the kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ilg_internal.h"
+#include "ilg_launch.h"
+
+using namespace ilg;
+
+struct ilg_ctx {
+  ilg_params p{};
+  int Q = 0;
+  uint32_t flip = 0;
+  uint64_t P_omega = 0, P_rest = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+  size_t nodes = 0;
+  uint16_t* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint64_t t = 0;
+  bool has_state = false;
+  uint32_t* d_tables = nullptr;            // thinning table, rest table
+  unsigned long long* d_fail = nullptr;    // first failing step, ~0 if none
+  unsigned long long* d_col = nullptr;     // Lx
+  unsigned long long* d_row = nullptr;     // Ly
+  unsigned long long* d_mass = nullptr;
+  int32_t* d_modes = nullptr;
+  double* d_res = nullptr;
+  uint32_t mode_cap = 0;
+  unsigned long long* h_word = nullptr;    // pinned 8-byte readback
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+ilg_status fail(ilg_ctx* c, ilg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+ilg_status cuda_fail(ilg_ctx* c, cudaError_t e, const char* what) {
+  const ilg_status s = (e == cudaErrorMemoryAllocation) ? ILG_E_OOM : ILG_E_CUDA;
+  return fail(c, s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define ILG_CUDA(c, call, what)                        \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+int num_vel(int lattice) { return lattice == ILG_D1Q3 ? 3 : 5; }
+
+uint32_t prob_mode(uint64_t P) {
+  if (P == 0) return kNever;
+  if (P == (uint64_t(1) << 32)) return kAlways;
+  return kTable;
+}
+
+std::string validate(const ilg_params& p) {
+  if (p.lattice != ILG_D1Q3 && p.lattice != ILG_D2Q5) return "lattice must be ILG_D1Q3 or ILG_D2Q5";
+  if (p.reserved != 0) return "reserved field must be 0";
+  const uint64_t Ly = p.lattice == ILG_D1Q3 ? 1 : p.Ly;
+  if (p.Lx < 3) return "Lx must be >= 3";
+  if (p.lattice == ILG_D2Q5 && p.Ly < 3) return "Ly must be >= 3";
+  if (uint64_t(p.Lx) * Ly >= (uint64_t(1) << 32)) return "Lx * Ly must be below 2^32";
+  if (!(p.omega_eff > 0.0 && p.omega_eff <= 2.0)) return "omega_eff must lie in (0, 2]";
+  if (p.lattice == ILG_D1Q3 && !(p.theta > 0.0 && p.theta < 1.0)) return "theta must lie in (0, 1) on D1Q3";
+  if (p.lattice == ILG_D2Q5 && !(p.theta > 0.0 && p.theta <= 0.5)) return "theta must lie in (0, 1/2] on D2Q5";
+  if (!(p.n0 >= 0.0) || !std::isfinite(p.n0)) return "n0 must be finite and >= 0";
+  if (!std::isfinite(p.amp)) return "amp must be finite";
+  if (p.mode_mx != 0 && p.mode_my != 0) return "the initial sine must be an axis mode";
+  if (p.lattice == ILG_D1Q3 && p.mode_my != 0) return "D1Q3 has no y mode";
+  return "";
+}
+
+int step_grid(const ilg_ctx* c) {
+  const size_t blocks = (c->nodes + 255) / 256;
+  const size_t cap = size_t(c->sms) * 8;
+  return int(blocks < cap ? blocks : cap);
+}
+
+StepArgs step_args(const ilg_ctx* c) {
+  StepArgs a{};
+  a.Lx = c->p.Lx;
+  a.Ly = c->Q == 3 ? 1 : c->p.Ly;
+  a.flip = c->flip;
+  a.omega_mode = prob_mode(c->P_omega);
+  a.rest_mode = prob_mode(c->P_rest);
+  a.key0 = uint32_t(c->p.seed);
+  a.key1 = uint32_t(c->p.seed >> 32);
+  a.replica = c->p.replica;
+  a.T_omega = c->d_tables;
+  a.T_rest = c->d_tables + kTableWords;
+  return a;
+}
+
+void free_ctx(ilg_ctx* c) {
+  cudaFree(c->buf[0]);
+  cudaFree(c->buf[1]);
+  cudaFree(c->d_tables);
+  cudaFree(c->d_fail);
+  cudaFree(c->d_col);
+  cudaFree(c->d_row);
+  cudaFree(c->d_mass);
+  cudaFree(c->d_modes);
+  cudaFree(c->d_res);
+  if (c->h_word) cudaFreeHost(c->h_word);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ilg_last_error(const ilg_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
+  if (!out) return fail(nullptr, ILG_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!params) return fail(nullptr, ILG_E_INVALID, "params is NULL");
+  const std::string bad = validate(*params);
+  if (!bad.empty()) return fail(nullptr, ILG_E_INVALID, bad);
+  ilg_ctx* c = new (std::nothrow) ilg_ctx();
+  if (!c) return fail(nullptr, ILG_E_OOM, "host allocation failed");
+  c->p = *params;
+  if (c->p.lattice == ILG_D1Q3) c->p.Ly = 1;
+  c->Q = num_vel(c->p.lattice);
+  c->stream = static_cast<cudaStream_t>(stream);
+  double w[5];
+  weights(c->p.lattice, c->p.theta, w);
+  double omega_star = c->p.omega_eff;
+  if (c->p.omega_eff > 1.0) {
+    c->flip = 1;
+    omega_star = 2.0 - c->p.omega_eff;
+  }
+  c->P_omega = quantise_probability(omega_star);
+  c->P_rest = quantise_probability(w[0]);
+  c->nodes = size_t(c->p.Lx) * c->p.Ly;
+
+  auto bail = [&](cudaError_t e, const char* what) {
+    cuda_fail(nullptr, e, what);
+    free_ctx(c);
+    delete c;
+    return (e == cudaErrorMemoryAllocation) ? ILG_E_OOM : ILG_E_CUDA;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) return bail(e, "cudaDeviceGetAttribute");
+  const size_t state_bytes = sizeof(uint16_t) * c->nodes * c->Q;
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMalloc(&c->buf[b], state_bytes);
+    if (e != cudaSuccess) return bail(e, "cudaMalloc state");
+  }
+  if ((e = cudaMalloc(&c->d_tables, sizeof(uint32_t) * 2 * kTableWords)) != cudaSuccess) return bail(e, "cudaMalloc tables");
+  if ((e = cudaMalloc(&c->d_fail, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc flag");
+  if ((e = cudaMalloc(&c->d_col, sizeof(unsigned long long) * c->p.Lx)) != cudaSuccess) return bail(e, "cudaMalloc sums");
+  if ((e = cudaMalloc(&c->d_row, sizeof(unsigned long long) * c->p.Ly)) != cudaSuccess) return bail(e, "cudaMalloc sums");
+  if ((e = cudaMalloc(&c->d_mass, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc mass");
+  if ((e = cudaMallocHost(&c->h_word, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMallocHost");
+
+  std::vector<uint32_t> tables(2 * kTableWords, 0u);
+  if (prob_mode(c->P_omega) == kTable) build_binomial_table(c->P_omega, tables.data());
+  if (prob_mode(c->P_rest) == kTable) build_binomial_table(c->P_rest, tables.data() + kTableWords);
+  e = cudaMemcpyAsync(c->d_tables, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return bail(e, "copy tables");
+  e = cudaMemsetAsync(c->d_fail, 0xFF, sizeof(unsigned long long), c->stream);
+  if (e != cudaSuccess) return bail(e, "reset flag");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return bail(e, "cudaStreamSynchronize");
+  *out = c;
+  return ILG_OK;
+}
+
+ilg_status ilg_destroy(ilg_ctx* c) {
+  if (!c) return ILG_OK;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+  delete c;
+  return ILG_OK;
+}
+
+ilg_status ilg_init(ilg_ctx* c) {
+  if (!c) return ILG_E_INVALID;
+  InitTables it;
+  std::string msg;
+  if (!build_init_tables(c->p, c->Q, &it, &msg)) return fail(c, ILG_E_INVALID, msg);
+  uint32_t *d_off = nullptr, *d_cnt = nullptr, *d_tab = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_off);
+    cudaFree(d_cnt);
+    cudaFree(d_tab);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&d_off, sizeof(uint32_t) * it.offset.size())) != cudaSuccess ||
+      (e = cudaMalloc(&d_cnt, sizeof(uint32_t) * it.count.size())) != cudaSuccess ||
+      (e = cudaMalloc(&d_tab, sizeof(uint32_t) * it.table.size())) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(c, e, "cudaMalloc init tables");
+  }
+  if ((e = cudaMemcpyAsync(d_off, it.offset.data(), sizeof(uint32_t) * it.offset.size(), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_cnt, it.count.data(), sizeof(uint32_t) * it.count.size(), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_tab, it.table.data(), sizeof(uint32_t) * it.table.size(), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(c, e, "copy init tables");
+  }
+  InitArgs a{};
+  a.Lx = c->p.Lx;
+  a.Ly = c->p.Ly;
+  a.period = it.period;
+  a.axis = 0;
+  a.mode = 0;
+  if (it.period > 1) {
+    const bool along_x = c->p.mode_mx != 0;
+    const int64_t L = it.period;
+    const int64_t mraw = along_x ? c->p.mode_mx : c->p.mode_my;
+    a.axis = along_x ? 1 : 2;
+    a.mode = uint32_t(((mraw % L) + L) % L);
+  }
+  a.weighted = c->p.init_weighted ? 1 : 0;
+  a.key0 = uint32_t(c->p.seed);
+  a.key1 = uint32_t(c->p.seed >> 32);
+  a.replica = c->p.replica;
+  a.offset = d_off;
+  a.count = d_cnt;
+  a.table = d_tab;
+  if ((e = launch_init(c->Q, a, c->buf[c->cur], step_grid(c), c->stream)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(c, e, "init kernel");
+  }
+  e = cudaStreamSynchronize(c->stream);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  c->t = 0;
+  c->has_state = true;
+  return ILG_OK;
+}
+
+static ilg_status set_state_impl(ilg_ctx* c, const uint16_t* src, size_t n, uint64_t t, cudaMemcpyKind kind) {
+  if (!c || !src) return ILG_E_INVALID;
+  if (n != c->nodes * c->Q) return fail(c, ILG_E_INVALID, "state size must be Q * Lx * Ly");
+  if (t >= (uint64_t(1) << 32)) return fail(c, ILG_E_INVALID, "t must be below 2^32");
+  ILG_CUDA(c, cudaMemcpyAsync(c->buf[c->cur], src, sizeof(uint16_t) * n, kind, c->stream), "copy state in");
+  ILG_CUDA(c, cudaStreamSynchronize(c->stream), "copy state in");
+  c->t = t;
+  c->has_state = true;
+  return ILG_OK;
+}
+
+static ilg_status get_state_impl(ilg_ctx* c, uint16_t* dst, size_t n, uint64_t* t, cudaMemcpyKind kind) {
+  if (!c || !dst) return ILG_E_INVALID;
+  if (!c->has_state) return fail(c, ILG_E_STATE, "no state: call ilg_init or ilg_set_state first");
+  if (n != c->nodes * c->Q) return fail(c, ILG_E_INVALID, "state size must be Q * Lx * Ly");
+  ILG_CUDA(c, cudaMemcpyAsync(dst, c->buf[c->cur], sizeof(uint16_t) * n, kind, c->stream), "copy state out");
+  ILG_CUDA(c, cudaStreamSynchronize(c->stream), "copy state out");
+  if (t) *t = c->t;
+  return ILG_OK;
+}
+
+ilg_status ilg_set_state(ilg_ctx* c, const uint16_t* host, size_t n, uint64_t t) {
+  return set_state_impl(c, host, n, t, cudaMemcpyHostToDevice);
+}
+ilg_status ilg_set_state_device(ilg_ctx* c, const uint16_t* dev, size_t n, uint64_t t) {
+  return set_state_impl(c, dev, n, t, cudaMemcpyDeviceToDevice);
+}
+ilg_status ilg_get_state(ilg_ctx* c, uint16_t* host, size_t n, uint64_t* t) {
+  return get_state_impl(c, host, n, t, cudaMemcpyDeviceToHost);
+}
+ilg_status ilg_get_state_device(ilg_ctx* c, uint16_t* dev, size_t n, uint64_t* t) {
+  return get_state_impl(c, dev, n, t, cudaMemcpyDeviceToDevice);
+}
+
+ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
+  if (!c) return ILG_E_INVALID;
+  if (!c->has_state) return fail(c, ILG_E_STATE, "no state: call ilg_init or ilg_set_state first");
+  if (c->t + T >= (uint64_t(1) << 32)) return fail(c, ILG_E_INVALID, "step counter would reach 2^32");
+  if (T == 0) return ILG_OK;
+  const StepArgs a = step_args(c);
+  const int grid = step_grid(c);
+  const int cur0 = c->cur;
+  const uint64_t t0 = c->t;
+  int cur = cur0;
+  for (uint32_t s = 0; s < T; ++s) {
+    cudaError_t e = launch_step_generic(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t0 + s), c->d_fail,
+                                        grid, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+    cur ^= 1;
+  }
+  ILG_CUDA(c, cudaMemcpyAsync(c->h_word, c->d_fail, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
+           "read overflow word");
+  ILG_CUDA(c, cudaStreamSynchronize(c->stream), "step");
+  const unsigned long long f = *c->h_word;
+  if (f != ~0ull) {
+    // step f failed: its input buffer still holds the state at step f
+    c->cur = cur0 ^ int((f - t0) & 1u);
+    c->t = f;
+    ILG_CUDA(c, cudaMemsetAsync(c->d_fail, 0xFF, sizeof(unsigned long long), c->stream), "reset flag");
+    ILG_CUDA(c, cudaStreamSynchronize(c->stream), "reset flag");
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "occupation above 65535 in step %llu; state kept at t = %llu", f, f);
+    return fail(c, ILG_E_OVERFLOW, buf);
+  }
+  c->cur = cur;
+  c->t = t0 + T;
+  return ILG_OK;
+}
+
+ilg_status ilg_observables(ilg_ctx* c, const int32_t* modes, uint32_t nmodes, uint64_t* t, uint64_t* mass,
+                           double* re, double* im, double* amp, double* Sk, int64_t* col_sums,
+                           int64_t* row_sums) {
+  if (!c) return ILG_E_INVALID;
+  if (!c->has_state) return fail(c, ILG_E_STATE, "no state: call ilg_init or ilg_set_state first");
+  if (nmodes && !modes) return fail(c, ILG_E_INVALID, "modes is NULL");
+  bool want_rows = row_sums != nullptr;
+  for (uint32_t i = 0; i < nmodes; ++i) {
+    const int32_t mx = modes[2 * i], my = modes[2 * i + 1];
+    if ((mx == 0) == (my == 0)) return fail(c, ILG_E_INVALID, "each mode must have exactly one nonzero component");
+    if (my != 0 && c->Q == 3) return fail(c, ILG_E_INVALID, "D1Q3 has no y modes");
+    if (my != 0) want_rows = true;
+  }
+  if (nmodes > c->mode_cap) {
+    cudaFree(c->d_modes);
+    cudaFree(c->d_res);
+    c->d_modes = nullptr;
+    c->d_res = nullptr;
+    c->mode_cap = 0;
+    ILG_CUDA(c, cudaMalloc(&c->d_modes, sizeof(int32_t) * 2 * nmodes), "cudaMalloc modes");
+    ILG_CUDA(c, cudaMalloc(&c->d_res, sizeof(double) * 4 * nmodes), "cudaMalloc modes");
+    c->mode_cap = nmodes;
+  }
+  const uint32_t Lx = c->p.Lx, Ly = c->p.Ly;
+  ILG_CUDA(c, cudaMemsetAsync(c->d_col, 0, sizeof(unsigned long long) * Lx, c->stream), "clear sums");
+  if (want_rows) ILG_CUDA(c, cudaMemsetAsync(c->d_row, 0, sizeof(unsigned long long) * Ly, c->stream), "clear sums");
+  if (nmodes)
+    ILG_CUDA(c, cudaMemcpyAsync(c->d_modes, modes, sizeof(int32_t) * 2 * nmodes, cudaMemcpyHostToDevice, c->stream),
+             "copy modes");
+  ILG_CUDA(c, launch_sums(c->Q, c->buf[c->cur], Lx, Ly, c->d_col, c->d_row, want_rows ? 1 : 0, c->stream), "sums kernel");
+  ILG_CUDA(c, launch_project(c->d_col, c->d_row, Lx, Ly, c->d_modes, nmodes, c->d_res, c->d_mass, c->stream),
+           "projection kernel");
+  std::vector<double> res(size_t(4) * nmodes);
+  unsigned long long M = 0;
+  if (nmodes)
+    ILG_CUDA(c, cudaMemcpyAsync(res.data(), c->d_res, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, c->stream),
+             "copy results");
+  ILG_CUDA(c, cudaMemcpyAsync(&M, c->d_mass, sizeof(M), cudaMemcpyDeviceToHost, c->stream), "copy mass");
+  if (col_sums)
+    ILG_CUDA(c, cudaMemcpyAsync(col_sums, c->d_col, sizeof(int64_t) * Lx, cudaMemcpyDeviceToHost, c->stream), "copy sums");
+  if (row_sums)
+    ILG_CUDA(c, cudaMemcpyAsync(row_sums, c->d_row, sizeof(int64_t) * Ly, cudaMemcpyDeviceToHost, c->stream), "copy sums");
+  ILG_CUDA(c, cudaStreamSynchronize(c->stream), "observables");
+  if (t) *t = c->t;
+  if (mass) *mass = M;
+  for (uint32_t i = 0; i < nmodes; ++i) {
+    if (re) re[i] = res[4 * i + 0];
+    if (im) im[i] = res[4 * i + 1];
+    if (amp) amp[i] = res[4 * i + 2];
+    if (Sk) Sk[i] = res[4 * i + 3];
+  }
+  return ILG_OK;
+}
+
+ilg_status ilg_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t n, void* stream) {
+  if (!ctr || !out) return fail(nullptr, ILG_E_INVALID, "NULL argument");
+  if (n == 0) return ILG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t *d_c = nullptr, *d_o = nullptr;
+  cudaError_t e = cudaMalloc(&d_c, sizeof(uint32_t) * 4 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&d_o, sizeof(uint32_t) * 4 * n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_c, ctr, sizeof(uint32_t) * 4 * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_philox(d_c, uint32_t(seed), uint32_t(seed >> 32), d_o, n, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_o, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_c);
+  cudaFree(d_o);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox probe");
+  return ILG_OK;
+}
+
+ilg_status ilg_binomial_table(uint64_t P, uint32_t* out) {
+  if (!out || P == 0 || P >= (uint64_t(1) << 32)) return fail(nullptr, ILG_E_INVALID, "P must lie in (0, 2^32)");
+  build_binomial_table(P, out);
+  return ILG_OK;
+}
+
+ilg_status ilg_poisson_table(double lambda, uint32_t* out, uint32_t cap, uint32_t* K) {
+  if (!out || !K || !(lambda >= 0.0) || lambda > kMaxMean) return fail(nullptr, ILG_E_INVALID, "bad argument");
+  std::vector<uint32_t> buf(kPoissonCap);
+  const uint32_t k = build_poisson_table(lambda, buf.data(), kPoissonCap);
+  if (k == 0 || k > cap) return fail(nullptr, ILG_E_INVALID, "table longer than cap");
+  std::memcpy(out, buf.data(), sizeof(uint32_t) * k);
+  *K = k;
+  return ILG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,37 @@
+// Internal declarations shared by the sources of libilg.so (host side).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ilg.h"
+
+namespace ilg {
+
+constexpr uint32_t kNmax = 64;                              // trials per binomial table row
+constexpr uint32_t kTableWords = kNmax * (kNmax + 1) / 2;   // 2080 entries
+constexpr uint32_t kPoissonCap = 4096;                       // entries per Poisson table
+constexpr double kMaxMean = 700.0;                           // largest initial mean
+
+// Philox purpose tags (top 8 bits of the fourth counter word).
+constexpr uint32_t kTagStep = 1;
+constexpr uint32_t kTagExt = 2;
+constexpr uint32_t kTagInit = 3;
+
+void build_binomial_table(uint64_t P, uint32_t* T);
+uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap);
+uint64_t quantise_probability(double p);
+void weights(int lattice, double theta, double* w);
+
+// Poisson tables of the initial state, one per (velocity class, phase residue).
+struct InitTables {
+  uint32_t period = 1;              // number of phase residues
+  int classes = 1;                  // 2 when means are weighted (rest, moving)
+  std::vector<uint32_t> offset;     // [classes * period] start in table
+  std::vector<uint32_t> count;      // [classes * period] entries
+  std::vector<uint32_t> table;      // concatenated CDF entries
+};
+bool build_init_tables(const ilg_params& p, int Q, InitTables* out, std::string* err);
+
+}  // namespace ilg

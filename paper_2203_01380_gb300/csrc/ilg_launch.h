@@ -1,0 +1,36 @@
+// Kernel launchers of libilg.so (implemented in ilg_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "ilg_device.cuh"
+
+namespace ilg {
+
+struct InitArgs {
+  uint32_t Lx, Ly;
+  uint32_t axis;      // 0 no sine mode, 1 along x, 2 along y
+  uint32_t mode;      // wave number reduced to [0, period)
+  uint32_t period;    // Lx, Ly, or 1
+  uint32_t weighted;  // 1: classes rest / moving
+  uint32_t key0, key1, replica;
+  const uint32_t* offset;  // [classes * period]
+  const uint32_t* count;   // [classes * period]
+  const uint32_t* table;
+};
+
+cudaError_t launch_step_generic(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out,
+                                uint32_t t, unsigned long long* fail, int grid, cudaStream_t s);
+cudaError_t launch_init(int Q, const InitArgs& a, uint16_t* out, int grid, cudaStream_t s);
+cudaError_t launch_sums(int Q, const uint16_t* in, uint32_t Lx, uint32_t Ly, unsigned long long* col,
+                        unsigned long long* row, int want_rows, cudaStream_t s);
+cudaError_t launch_project(const unsigned long long* col, const unsigned long long* row, uint32_t Lx,
+                           uint32_t Ly, const int32_t* modes, uint32_t nmodes, double* res,
+                           unsigned long long* mass, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, size_t n,
+                          cudaStream_t s);
+
+}  // namespace ilg

@@ -1,0 +1,126 @@
+// Host-side construction of the integer tables the kernels read.
+//
+// Compiled with -ffp-contract=off: the Poisson tables and the initial means are
+// defined by a fixed sequence of IEEE double operations and libm calls, and must
+// come out the same on every host.
+#include "ilg_internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace ilg {
+
+// Integer CDF rows of Binomial(n, P/2^32), n = 1..kNmax.  The pmf of n trials is
+// carried in fixed point with one = 2^63; each row follows from the previous one
+// by Pascal's rule with the two products floored, and the CDF entry of (n, k) is
+// the running pmf sum shifted down to 32 fractional bits.
+void build_binomial_table(uint64_t P, uint32_t* T) {
+  const uint64_t Pq = (uint64_t(1) << 32) - P;
+  uint64_t pmf[kNmax + 2];
+  uint64_t next[kNmax + 2];
+  std::memset(pmf, 0, sizeof(pmf));
+  pmf[0] = uint64_t(1) << 63;
+  for (uint32_t n = 1; n <= kNmax; ++n) {
+    next[0] = uint64_t((static_cast<unsigned __int128>(pmf[0]) * Pq) >> 32);
+    for (uint32_t k = 1; k < n; ++k) {
+      unsigned __int128 a = (static_cast<unsigned __int128>(pmf[k]) * Pq) >> 32;
+      unsigned __int128 b = (static_cast<unsigned __int128>(pmf[k - 1]) * P) >> 32;
+      next[k] = uint64_t(a + b);
+    }
+    next[n] = uint64_t((static_cast<unsigned __int128>(pmf[n - 1]) * P) >> 32);
+    std::memcpy(pmf, next, sizeof(uint64_t) * (n + 1));
+    uint32_t* row = T + n * (n - 1) / 2;
+    uint64_t run = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+      run += pmf[k];
+      row[k] = uint32_t(run >> 31);
+    }
+  }
+}
+
+// Poisson(lambda) CDF scaled to 2^32, floored, saturating at 2^32 - 1, up to and
+// including the first saturated entry.  Returns the entry count, 0 if above cap.
+uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap) {
+  double term = std::exp(-lambda);
+  double cdf = term;
+  for (uint32_t k = 0; k < cap; ++k) {
+    if (k != 0) {
+      term = term * lambda / static_cast<double>(k);
+      cdf = cdf + term;
+    }
+    const double s = std::floor(cdf * 4294967296.0);
+    const uint32_t v = (s >= 4294967295.0) ? 0xFFFFFFFFu : static_cast<uint32_t>(s);
+    T[k] = v;
+    if (v == 0xFFFFFFFFu) return k + 1;
+  }
+  return 0;
+}
+
+uint64_t quantise_probability(double p) {
+  double v = std::floor(p * 4294967296.0 + 0.5);
+  if (v <= 0.0) return 0;
+  if (v >= 4294967296.0) return uint64_t(1) << 32;
+  return static_cast<uint64_t>(v);
+}
+
+void weights(int lattice, double theta, double* w) {
+  if (lattice == ILG_D1Q3) {
+    w[0] = 1.0 - theta;
+    w[1] = w[2] = theta / 2.0;
+  } else {
+    w[0] = 1.0 - 2.0 * theta;
+    w[1] = w[2] = w[3] = w[4] = theta / 2.0;
+  }
+}
+
+// Sine value of the initial profile for phase residue r of a mode of period L.
+static double profile_sine(uint32_t r, uint32_t L) {
+  return std::sin((6.283185307179586 * static_cast<double>(r)) / static_cast<double>(L));
+}
+
+// Initial mean of velocity class c (0 = rest, 1 = moving; only class 0 when the
+// means are not weighted) at phase residue r.
+static double initial_mean(const ilg_params& p, int Q, int cls, uint32_t r, uint32_t L) {
+  const double s = (p.amp != 0.0 && L != 0) ? profile_sine(r, L) : 0.0;
+  if (p.init_weighted) {
+    double w[5];
+    weights(p.lattice, p.theta, w);
+    const double wc = cls == 0 ? w[0] : w[1];
+    return wc * (static_cast<double>(Q) * p.n0 + p.amp * s);
+  }
+  return p.n0 + (p.amp * s) / static_cast<double>(Q);
+}
+
+bool build_init_tables(const ilg_params& p, int Q, InitTables* out, std::string* err) {
+  uint32_t L = 1;  // period of the phase residue
+  if (p.amp != 0.0 && p.mode_mx != 0) L = p.Lx;
+  else if (p.amp != 0.0 && p.mode_my != 0) L = (p.lattice == ILG_D1Q3) ? 1 : p.Ly;
+  const int classes = p.init_weighted ? 2 : 1;
+  out->period = L;
+  out->classes = classes;
+  out->offset.assign(size_t(classes) * L, 0);
+  out->count.assign(size_t(classes) * L, 0);
+  out->table.clear();
+  std::vector<uint32_t> buf(kPoissonCap);
+  for (int c = 0; c < classes; ++c) {
+    for (uint32_t r = 0; r < L; ++r) {
+      const double lam = initial_mean(p, Q, c, r, L);
+      if (!(lam >= 0.0) || lam > kMaxMean) {
+        *err = "initial mean " + std::to_string(lam) + " outside [0, 700]";
+        return false;
+      }
+      const uint32_t K = build_poisson_table(lam, buf.data(), kPoissonCap);
+      if (K == 0) {
+        *err = "Poisson table of mean " + std::to_string(lam) + " exceeds its cap";
+        return false;
+      }
+      out->offset[size_t(c) * L + r] = static_cast<uint32_t>(out->table.size());
+      out->count[size_t(c) * L + r] = K;
+      out->table.insert(out->table.end(), buf.begin(), buf.begin() + K);
+    }
+  }
+  return true;
+}
+
+}  // namespace ilg
