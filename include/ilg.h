@@ -82,7 +82,7 @@ typedef struct ilg_ctx ilg_ctx;
 
 /* Create a context for one lattice: validates params, allocates two state buffers
  * (2 * Q * Lx * Ly uint16) plus tables and reduction scratch on the current device,
- * and builds the integer CDF tables of the collision.  *out is NULL on failure. */
+ * and builds the integer alias tables of the collision.  *out is NULL on failure. */
 ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out);
 
 /* Release every device allocation of the context (after synchronising its stream). */
@@ -129,12 +129,17 @@ ilg_status ilg_observables(ilg_ctx* ctx, const int32_t* modes, uint32_t nmodes, 
  * ilg_philox: n Philox4x32-10 blocks computed on the device; ctr (4n words) and out
  *   (4n words) are host arrays; key = (seed lo32, seed hi32).
  * ilg_binomial_table: the 2080-entry integer CDF table (rows n = 1..64, row n at
- *   offset n(n-1)/2) the collision uses for probability P / 2^32, 0 < P < 2^32; host
- *   only, no device work.
+ *   offset n(n-1)/2) of Binomial(n, P / 2^32), 0 < P < 2^32; host only.
+ * ilg_alias_table: the 2145-entry alias tables (rows n = 0..64, row n at offset
+ *   n(n+1)/2, column j of row n at offset n(n+1)/2 + j) the collision draws
+ *   Binomial(n, P / 2^32) with: a draw u takes column j = floor(u (n+1) / 2^32) and
+ *   yields j if u < thr[.], else alias[.]; they realise the CDF table's integer pmf
+ *   exactly.  Host only.
  * ilg_poisson_table: the Poisson CDF table of the initial state for mean lambda;
  *   writes at most cap entries and their count to *K; host only. */
 ilg_status ilg_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t n, void* stream);
 ilg_status ilg_binomial_table(uint64_t P, uint32_t* out);
+ilg_status ilg_alias_table(uint64_t P, uint32_t* thr, uint32_t* alias);
 ilg_status ilg_poisson_table(double lambda, uint32_t* out, uint32_t cap, uint32_t* K);
 
 #ifdef __cplusplus

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 shares no code with the CUDA library (``paper_2203_01380_gb300``) and neither
 imports the other.
 
-The integer work (Philox4x32-10, binomial and Poisson tables, the time step,
+The integer work (Philox4x32-10, binomial pmf and alias tables, Poisson tables, the time step,
 the initial state and the integer sums) lives in ``ilg_oracle.c``, compiled with
 plain ``gcc`` into ``liboracle.so`` beside it.  The floating-point projections
 (measured amplitude A^LG of Sec. V and the structure factor) are evaluated here
@@ -55,7 +55,8 @@ class _StepParams(ctypes.Structure):
         ("lattice", ctypes.c_int32), ("Lx", ctypes.c_uint32), ("Ly", ctypes.c_uint32),
         ("flip", ctypes.c_int32), ("P_omega", ctypes.c_uint64), ("P_rest", ctypes.c_uint64),
         ("seed", ctypes.c_uint64), ("replica", ctypes.c_uint32),
-        ("T_omega", ctypes.c_void_p), ("T_rest", ctypes.c_void_p),
+        ("thr_omega", ctypes.c_void_p), ("alias_omega", ctypes.c_void_p),
+        ("thr_rest", ctypes.c_void_p), ("alias_rest", ctypes.c_void_p),
     ]
 
 
@@ -83,6 +84,9 @@ def lib():
         L.oracle_philox.restype = None
         L.oracle_binomial_table.argtypes = [ctypes.c_uint64, ctypes.c_uint32, u32p]
         L.oracle_binomial_table.restype = None
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        L.oracle_alias_table.argtypes = [ctypes.c_uint64, ctypes.c_uint32, u32p, u8p]
+        L.oracle_alias_table.restype = None
         L.oracle_poisson_table.argtypes = [ctypes.c_double, u32p, ctypes.c_uint32]
         L.oracle_poisson_table.restype = ctypes.c_uint32
         L.oracle_step_region.argtypes = [ctypes.POINTER(_StepParams), u16p, u16p, ctypes.c_uint32,
@@ -139,6 +143,19 @@ def binomial_table(P: int, nmax: int = NMAX) -> np.ndarray:
     return T
 
 
+ALIAS_ENTRIES = (NMAX + 1) * (NMAX + 2) // 2   # rows n = 0..NMAX, n + 1 columns each
+
+
+def alias_table(P: int, nmax: int = NMAX):
+    """(thr, alias) of the alias tables of Binomial(n, P/2^32), n = 0..nmax; row n at
+    offset n(n+1)/2."""
+    n_ent = (nmax + 1) * (nmax + 2) // 2
+    thr = np.zeros(n_ent, dtype=np.uint32)
+    al = np.zeros(n_ent, dtype=np.uint8)
+    lib().oracle_alias_table(ctypes.c_uint64(P), nmax, thr, al)
+    return thr, al
+
+
 def poisson_table(lam: float) -> np.ndarray:
     T = np.zeros(POISSON_KMAX, dtype=np.uint32)
     K = lib().oracle_poisson_table(lam, T, POISSON_KMAX)
@@ -167,12 +184,14 @@ class Lattice:
         self.w = weights(lattice, self.theta)
         self.P_omega = quantise(self.omega_star)
         self.P_rest = quantise(self.w[0])
-        self._T_omega = binomial_table(self.P_omega) if 0 < self.P_omega < TWO32 else np.zeros(1, np.uint32)
-        self._T_rest = binomial_table(self.P_rest) if 0 < self.P_rest < TWO32 else np.zeros(1, np.uint32)
+        none = (np.zeros(1, np.uint32), np.zeros(1, np.uint8))
+        self._A_omega = alias_table(self.P_omega) if 0 < self.P_omega < TWO32 else none
+        self._A_rest = alias_table(self.P_rest) if 0 < self.P_rest < TWO32 else none
 
     def _sp(self):
         return _StepParams(self.lattice, self.Lx, self.Ly, self.flip, self.P_omega, self.P_rest,
-                           self.seed, self.replica, self._T_omega.ctypes.data, self._T_rest.ctypes.data)
+                           self.seed, self.replica, self._A_omega[0].ctypes.data, self._A_omega[1].ctypes.data,
+                           self._A_rest[0].ctypes.data, self._A_rest[1].ctypes.data)
 
     def _ip(self):
         return _InitParams(self.lattice, self.Lx, self.Ly, self.n0, self.amp, self.mode_mx,

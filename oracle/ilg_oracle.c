@@ -29,9 +29,9 @@
  * Randomness: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here
  * from its published round function.  Counter = (node id, t, replica,
  * tag<<24 | block), key = (seed lo, seed hi); word d of a stream is lane d&3 of
- * block d>>2.  Binomial draws invert an integer CDF table that is defined by
- * an integer Pascal recurrence (below), so both implementations produce the
- * same bits without floating point.
+ * block d>>2.  Binomial draws go through an alias table built in integers from
+ * a pmf that is defined by an integer Pascal recurrence (below), so both
+ * implementations produce the same bits without floating point.
  */
 #include <math.h>
 #include <stdint.h>
@@ -113,12 +113,67 @@ void oracle_binomial_table(uint64_t P, uint32_t nmax, uint32_t *T) {
   free(g);
 }
 
-/* Binomial(n, P/2^32) for n <= OR_NMAX by inversion: the number of k < n with u >= T[n][k] */
-static uint32_t binomial_invert(const uint32_t *T, uint32_t n, uint32_t u) {
-  const uint32_t *row = T + n * (n - 1) / 2;
-  uint32_t k = 0;
-  while (k < n && u >= row[k]) ++k;
-  return k;
+/*
+ * Alias table (Walker's method, Vose's construction in integers) over the same
+ * integer pmf.  Row n (0 <= n <= nmax) has n+1 columns j, stored at offset
+ * n(n+1)/2.  Outcome weights: W_0 = T[n][0], W_k = T[n][k] - T[n][k-1],
+ * W_n = 2^32 - T[n][n-1] (W_0 = 2^32 for n = 0); they sum to 2^32.  Column j
+ * covers the draws a_j <= u < a_{j+1}, a_j = ceil(j 2^32 / (n+1)), size s_j.
+ * A draw u picks column j = floor(u (n+1) / 2^32) and yields j if u < thr[j],
+ * else alias[j].
+ * Construction: columns with W_j = s_j are full (alias = j); the others go on a
+ * "small" (W_j < s_j) or "large" (W_j > s_j) stack, pushed in increasing j.
+ * While both stacks are non-empty: pop l (small) and g (large) from their tops;
+ * column l gives its first W_l draws to l (thr[l] = a_l + W_l) and the rest to g
+ * (alias[l] = g); W_g drops by s_l - W_l and g is pushed back on the stack its
+ * new weight belongs to (or is full).  Every outcome's weight is realised exactly.
+ */
+void oracle_alias_table(uint64_t P, uint32_t nmax, uint32_t *thr, uint8_t *alias) {
+  uint32_t *T = (uint32_t *)malloc(sizeof(uint32_t) * (nmax * (nmax + 1) / 2 + 1));
+  uint64_t *W = (uint64_t *)malloc(sizeof(uint64_t) * (nmax + 1));
+  uint32_t *small = (uint32_t *)malloc(sizeof(uint32_t) * (nmax + 1));
+  uint32_t *large = (uint32_t *)malloc(sizeof(uint32_t) * (nmax + 1));
+  uint64_t *a = (uint64_t *)malloc(sizeof(uint64_t) * (nmax + 2));
+  oracle_binomial_table(P, nmax, T);
+  for (uint32_t n = 0; n <= nmax; ++n) {
+    const uint32_t *row = T + (n ? n * (n - 1) / 2 : 0);
+    uint32_t *th = thr + n * (n + 1) / 2;
+    uint8_t *al = alias + n * (n + 1) / 2;
+    uint64_t prev = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+      W[k] = (uint64_t)row[k] - prev;
+      prev = row[k];
+    }
+    W[n] = ((uint64_t)1 << 32) - prev;
+    for (uint32_t j = 0; j <= n + 1; ++j) a[j] = (((uint64_t)j << 32) + n) / (n + 1);
+    uint32_t ns = 0, nl = 0;
+    for (uint32_t j = 0; j <= n; ++j) {
+      uint64_t s = a[j + 1] - a[j];
+      th[j] = 0;
+      al[j] = (uint8_t)j;
+      if (W[j] < s) small[ns++] = j;
+      else if (W[j] > s) large[nl++] = j;
+    }
+    while (ns > 0 && nl > 0) {
+      uint32_t l = small[--ns];
+      uint32_t g = large[--nl];
+      uint64_t sl = a[l + 1] - a[l];
+      th[l] = (uint32_t)(a[l] + W[l]);
+      al[l] = (uint8_t)g;
+      W[g] -= sl - W[l];
+      uint64_t sg = a[g + 1] - a[g];
+      if (W[g] < sg) small[ns++] = g;
+      else if (W[g] > sg) large[nl++] = g;
+    }
+  }
+  free(T); free(W); free(small); free(large); free(a);
+}
+
+/* Binomial(n, P/2^32) for n <= OR_NMAX: one draw through row n of the alias table */
+static uint32_t binomial_draw(const uint32_t *thr, const uint8_t *alias, uint32_t n, uint32_t u) {
+  uint32_t off = n * (n + 1) / 2;
+  uint32_t j = (uint32_t)(((uint64_t)u * (n + 1)) >> 32);
+  return u < thr[off + j] ? j : alias[off + j];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -133,8 +188,10 @@ typedef struct {
   uint64_t P_rest;    /* round(w_0 * 2^32) in [0, 2^32] */
   uint64_t seed;
   uint32_t replica;
-  const uint32_t *T_omega; /* binomial table for P_omega (unused if P_omega is 0 or 2^32) */
-  const uint32_t *T_rest;  /* binomial table for P_rest (unused if P_rest is 0 or 2^32) */
+  const uint32_t *thr_omega; /* alias table of P_omega (unused if P_omega is 0 or 2^32) */
+  const uint8_t *alias_omega;
+  const uint32_t *thr_rest;  /* alias table of P_rest (unused if P_rest is 0 or 2^32) */
+  const uint8_t *alias_rest;
 } oracle_step_params;
 
 static int num_vel(int32_t lattice) { return lattice == 1 ? 3 : 5; }
@@ -160,8 +217,8 @@ static uint32_t ext_next(ext_reader *e) {
 
 /* Binomial(m, P/2^32): chunks of at most OR_NMAX trials; the first chunk uses
  * the word of its fixed slot, every further chunk the next extension word. */
-static uint32_t binomial_chunked(uint64_t P, const uint32_t *T, uint32_t m, uint32_t slot_word,
-                                 ext_reader *ext) {
+static uint32_t binomial_chunked(uint64_t P, const uint32_t *thr, const uint8_t *alias, uint32_t m,
+                                 uint32_t slot_word, ext_reader *ext) {
   if (P == 0) return 0;
   if (P == ((uint64_t)1 << 32)) return m;
   uint32_t r = 0, left = m;
@@ -170,7 +227,7 @@ static uint32_t binomial_chunked(uint64_t P, const uint32_t *T, uint32_t m, uint
     uint32_t c = left < OR_NMAX ? left : OR_NMAX;
     uint32_t u = first ? slot_word : ext_next(ext);
     first = 0;
-    r += binomial_invert(T, c, u);
+    r += binomial_draw(thr, alias, c, u);
     left -= c;
   }
   return r;
@@ -194,12 +251,12 @@ static void collide_node(const oracle_step_params *p, uint32_t node, uint32_t t,
   /* thinning: r_i = Binomial(m_i, omega*), slot word i */
   uint32_t removed_total = 0;
   for (int i = 0; i < Q; ++i) {
-    uint32_t r = binomial_chunked(p->P_omega, p->T_omega, m[i], W[i], &ext);
+    uint32_t r = binomial_chunked(p->P_omega, p->thr_omega, p->alias_omega, m[i], W[i], &ext);
     out[i] = m[i] - r;
     removed_total += r;
   }
   /* rest share: R_0 = Binomial(R, w_0), slot word Q */
-  uint32_t to_rest = binomial_chunked(p->P_rest, p->T_rest, removed_total, W[Q], &ext);
+  uint32_t to_rest = binomial_chunked(p->P_rest, p->thr_rest, p->alias_rest, removed_total, W[Q], &ext);
   out[0] += to_rest;
   uint32_t moving = removed_total - to_rest;
 

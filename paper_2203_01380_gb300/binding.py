@@ -63,10 +63,11 @@ _lib.ilg_observables.argtypes = [_vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctype
                                  ctypes.POINTER(ctypes.c_uint64), _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.ilg_philox.argtypes = [_u32p, ctypes.c_uint64, _u32p, ctypes.c_size_t, _vp]
 _lib.ilg_binomial_table.argtypes = [ctypes.c_uint64, _u32p]
+_lib.ilg_alias_table.argtypes = [ctypes.c_uint64, _u32p, _u32p]
 _lib.ilg_poisson_table.argtypes = [ctypes.c_double, _u32p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
 for _f in ("ilg_create", "ilg_destroy", "ilg_init", "ilg_set_state", "ilg_set_state_device", "ilg_get_state",
            "ilg_get_state_device", "ilg_step", "ilg_observables", "ilg_philox", "ilg_binomial_table",
-           "ilg_poisson_table"):
+           "ilg_alias_table", "ilg_poisson_table"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -187,6 +188,13 @@ def binomial_table(P: int) -> np.ndarray:
     out = np.zeros(2080, dtype=np.uint32)
     _check(_lib.ilg_binomial_table(int(P), out))
     return out
+
+
+def alias_table(P: int):
+    thr = np.zeros(2145, dtype=np.uint32)
+    al = np.zeros(2145, dtype=np.uint32)
+    _check(_lib.ilg_alias_table(int(P), thr, al))
+    return thr, al
 
 
 def poisson_table(lam: float, cap: int = 4096) -> np.ndarray:

@@ -86,8 +86,15 @@ std::string validate(const ilg_params& p) {
 
 int step_grid(const ilg_ctx* c) {
   const size_t blocks = (c->nodes + 255) / 256;
-  const size_t cap = size_t(c->sms) * 8;
+  const size_t cap = size_t(c->sms) * 4;
   return int(blocks < cap ? blocks : cap);
+}
+
+// row-tiled step: one block per row at a time, three blocks per SM
+int vec_grid(const ilg_ctx* c) {
+  const size_t rows = c->p.Ly;
+  const size_t cap = size_t(c->sms) * 3;
+  return int(rows < cap ? rows : cap);
 }
 
 StepArgs step_args(const ilg_ctx* c) {
@@ -100,8 +107,14 @@ StepArgs step_args(const ilg_ctx* c) {
   a.key0 = uint32_t(c->p.seed);
   a.key1 = uint32_t(c->p.seed >> 32);
   a.replica = c->p.replica;
-  a.T_omega = c->d_tables;
-  a.T_rest = c->d_tables + kTableWords;
+  a.tables = c->d_tables;
+  uint32_t k0 = a.key0, k1 = a.key1;
+  for (int r = 0; r < 10; ++r) {
+    a.rk[2 * r] = k0;
+    a.rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
   return a;
 }
 
@@ -164,16 +177,20 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
     e = cudaMalloc(&c->buf[b], state_bytes);
     if (e != cudaSuccess) return bail(e, "cudaMalloc state");
   }
-  if ((e = cudaMalloc(&c->d_tables, sizeof(uint32_t) * 2 * kTableWords)) != cudaSuccess) return bail(e, "cudaMalloc tables");
+  static_assert(kBlockWords == kDevBlockWords, "table block layout");
+  if ((e = cudaMalloc(&c->d_tables, sizeof(uint32_t) * kBlockWords)) != cudaSuccess) return bail(e, "cudaMalloc tables");
   if ((e = cudaMalloc(&c->d_fail, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc flag");
   if ((e = cudaMalloc(&c->d_col, sizeof(unsigned long long) * c->p.Lx)) != cudaSuccess) return bail(e, "cudaMalloc sums");
   if ((e = cudaMalloc(&c->d_row, sizeof(unsigned long long) * c->p.Ly)) != cudaSuccess) return bail(e, "cudaMalloc sums");
   if ((e = cudaMalloc(&c->d_mass, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc mass");
   if ((e = cudaMallocHost(&c->h_word, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMallocHost");
 
-  std::vector<uint32_t> tables(2 * kTableWords, 0u);
-  if (prob_mode(c->P_omega) == kTable) build_binomial_table(c->P_omega, tables.data());
-  if (prob_mode(c->P_rest) == kTable) build_binomial_table(c->P_rest, tables.data() + kTableWords);
+  std::vector<uint32_t> tables(kBlockWords, 0u);
+  AliasEntry* alias = reinterpret_cast<AliasEntry*>(tables.data());
+  if (prob_mode(c->P_omega) == kTable) build_alias_table(c->P_omega, alias);
+  if (prob_mode(c->P_rest) == kTable) build_alias_table(c->P_rest, alias + kAliasEntries);
+  if ((e = prepare_step_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
+  if ((e = prepare_step_vec_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   e = cudaMemcpyAsync(c->d_tables, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return bail(e, "copy tables");
   e = cudaMemsetAsync(c->d_fail, 0xFF, sizeof(unsigned long long), c->stream);
@@ -288,13 +305,16 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   if (c->t + T >= (uint64_t(1) << 32)) return fail(c, ILG_E_INVALID, "step counter would reach 2^32");
   if (T == 0) return ILG_OK;
   const StepArgs a = step_args(c);
-  const int grid = step_grid(c);
+  const bool vec = (c->p.Lx % step_vec_width()) == 0;
+  const int grid = vec ? vec_grid(c) : step_grid(c);
   const int cur0 = c->cur;
   const uint64_t t0 = c->t;
   int cur = cur0;
   for (uint32_t s = 0; s < T; ++s) {
-    cudaError_t e = launch_step_generic(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t0 + s), c->d_fail,
-                                        grid, c->stream);
+    cudaError_t e = vec ? launch_step_vec(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t0 + s), c->d_fail,
+                                          grid, c->stream)
+                        : launch_step(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t0 + s), c->d_fail, grid,
+                                      c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
     cur ^= 1;
   }
@@ -391,6 +411,17 @@ ilg_status ilg_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t 
 ilg_status ilg_binomial_table(uint64_t P, uint32_t* out) {
   if (!out || P == 0 || P >= (uint64_t(1) << 32)) return fail(nullptr, ILG_E_INVALID, "P must lie in (0, 2^32)");
   build_binomial_table(P, out);
+  return ILG_OK;
+}
+
+ilg_status ilg_alias_table(uint64_t P, uint32_t* thr, uint32_t* alias) {
+  if (!thr || !alias || P == 0 || P >= (uint64_t(1) << 32)) return fail(nullptr, ILG_E_INVALID, "P must lie in (0, 2^32)");
+  std::vector<AliasEntry> t(kAliasEntries);
+  build_alias_table(P, t.data());
+  for (uint32_t i = 0; i < kAliasEntries; ++i) {
+    thr[i] = t[i].thr;
+    alias[i] = t[i].alias;
+  }
   return ILG_OK;
 }
 

@@ -1,5 +1,5 @@
 // Device building blocks of the lattice-gas step: Philox4x32-10 and the
-// sampling collision of one node (flip, binomial thinning, multinomial
+// sampling collision of one node (binomial thinning, multinomial
 // redistribution), in integer arithmetic only.
 #pragma once
 
@@ -8,7 +8,9 @@
 namespace ilg {
 
 constexpr uint32_t kDevNmax = 64;
-constexpr uint32_t kDevTableWords = kDevNmax * (kDevNmax + 1) / 2;
+constexpr uint32_t kDevAliasEntries = (kDevNmax + 1) * (kDevNmax + 2) / 2;  // rows n = 0..64
+// table block: alias table (thinning) | alias table (rest), one uint2 {thr, alias} per column
+constexpr uint32_t kDevBlockWords = 2 * kDevAliasEntries * 2;
 constexpr uint32_t kDevTagStep = 1u << 24;
 constexpr uint32_t kDevTagExt = 2u << 24;
 constexpr uint32_t kDevTagInit = 3u << 24;
@@ -24,8 +26,8 @@ struct StepArgs {
   uint32_t rest_mode;    // same for the rest weight w_0
   uint32_t key0, key1;   // Philox key = seed
   uint32_t replica;
-  const uint32_t* T_omega;  // device, kDevTableWords entries
-  const uint32_t* T_rest;
+  const uint32_t* tables;   // device, kDevBlockWords words (layout above)
+  uint32_t rk[20];          // round keys (key0 + r W0, key1 + r W1), r = 0..9
 };
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
@@ -45,6 +47,19 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// Same function with the ten round keys precomputed (rk[2r], rk[2r+1]); the keys
+// then come straight from the kernel's parameter bank.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = uint64_t(0xD2511F53u) * c.x;
+    const uint64_t p1 = uint64_t(0xCD9E8D57u) * c.z;
+    c = make_uint4(uint32_t(p1 >> 32) ^ c.y ^ rk[2 * r], uint32_t(p1), uint32_t(p0 >> 32) ^ c.w ^ rk[2 * r + 1],
+                   uint32_t(p0));
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint32_t lane_of(const uint4& b, uint32_t i) {
   return i == 0 ? b.x : (i == 1 ? b.y : (i == 2 ? b.z : b.w));
 }
@@ -58,7 +73,7 @@ struct ExtStream {
 __device__ __forceinline__ uint32_t ext_word(const StepArgs& a, ExtStream& e) {
   const uint32_t b = e.next >> 2;
   if (b != e.cached) {
-    e.blk = philox(make_uint4(e.node, e.t, a.replica, kDevTagExt | b), a.key0, a.key1);
+    e.blk = philox_rk(make_uint4(e.node, e.t, a.replica, kDevTagExt | b), a.rk);
     e.cached = b;
   }
   const uint32_t w = lane_of(e.blk, e.next & 3u);
@@ -66,50 +81,59 @@ __device__ __forceinline__ uint32_t ext_word(const StepArgs& a, ExtStream& e) {
   return w;
 }
 
-// Binomial(n, P) for n <= 64 by inversion of the integer CDF row n.
-__device__ __forceinline__ uint32_t binomial_row(const uint32_t* T, uint32_t n, uint32_t u) {
-  const uint32_t* row = T + n * (n - 1) / 2;
-  uint32_t k = 0;
-  while (k < n && u >= row[k]) ++k;
-  return k;
+// The two alias tables of the block (shared memory).
+__device__ __forceinline__ const uint2* thinning_table(const uint32_t* s) {
+  return reinterpret_cast<const uint2*>(s);
+}
+__device__ __forceinline__ const uint2* rest_table(const uint32_t* s) {
+  return reinterpret_cast<const uint2*>(s) + kDevAliasEntries;
 }
 
-// Binomial(m, P): chunks of 64 trials, the first with the slot word, every further
-// chunk with the next extension word.
-__device__ __forceinline__ uint32_t binomial(uint32_t mode, const uint32_t* T, uint32_t m,
-                                             uint32_t slot, const StepArgs& a, ExtStream& e) {
-  if (mode == kNever) return 0;
+// Binomial(n, P/2^32) for 0 <= n <= 64 with one draw u: column j = floor(u (n+1) / 2^32)
+// of row n (entries n(n+1)/2 ..); j if u is below the column's threshold, else its alias.
+__device__ __forceinline__ uint32_t binomial_alias(const uint2* A, uint32_t n, uint32_t u) {
+  const uint32_t j = __umulhi(u, n + 1);
+  const uint2 e = A[((n * (n + 1)) >> 1) + j];
+  return u < e.x ? j : e.y;
+}
+
+// Binomial(m, P) for any m: chunks of 64 trials, the first with the slot word,
+// every further chunk with the next extension word.
+__device__ __forceinline__ uint32_t binomial(uint32_t mode, const uint2* A, uint32_t m, uint32_t slot,
+                                             const StepArgs& a, ExtStream& e) {
+  if (mode == kNever || m == 0) return 0;
   if (mode == kAlways) return m;
-  if (m <= kDevNmax) return m ? binomial_row(T, m, slot) : 0;
-  uint32_t r = binomial_row(T, kDevNmax, slot);
+  if (m <= kDevNmax) return binomial_alias(A, m, slot);
+  uint32_t r = binomial_alias(A, kDevNmax, slot);
   uint32_t left = m - kDevNmax;
   while (left > 0) {
     const uint32_t c = left < kDevNmax ? left : kDevNmax;
-    r += binomial_row(T, c, ext_word(a, e));
+    r += binomial_alias(A, c, ext_word(a, e));
     left -= c;
   }
   return r;
 }
 
-// The collision of one node.  m = occupations after the flip; out = n'.
-// Tables sTo (thinning) and sTr (rest weight) are usually in shared memory.
+// The general collision of one node (any occupations).  m = occupations after
+// the flip; out = n'.  s = the table block (usually in shared memory).
 template <int Q>
-__device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* sTo, const uint32_t* sTr,
-                                        uint32_t node, uint32_t t, const uint32_t (&m)[Q],
-                                        uint32_t (&out)[Q]) {
-  const uint4 b0 = philox(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.key0, a.key1);
-  const uint4 b1 = philox(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.key0, a.key1);
+__device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
+                                        const uint32_t (&m)[Q], uint32_t (&out)[Q]) {
+  const uint2* to = thinning_table(s);
+  const uint2* tr = rest_table(s);
+  const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
+  const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
   const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
   ExtStream e{node, t, 0u, 0xFFFFFFFFu, make_uint4(0, 0, 0, 0)};
 
   uint32_t removed = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const uint32_t r = binomial(a.omega_mode, sTo, m[i], W[i], a, e);
+    const uint32_t r = binomial(a.omega_mode, to, m[i], W[i], a, e);
     out[i] = m[i] - r;
     removed += r;
   }
-  const uint32_t to_rest = binomial(a.rest_mode, sTr, removed, W[Q], a, e);
+  const uint32_t to_rest = binomial(a.rest_mode, tr, removed, W[Q], a, e);
   out[0] += to_rest;
   uint32_t moving = removed - to_rest;
   bool first = true;
@@ -117,8 +141,8 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* sTo, 
     const uint32_t c = moving < 32 ? moving : 32;
     const uint32_t mask = c == 32 ? 0xFFFFFFFFu : ((1u << c) - 1u);
     if constexpr (Q == 3) {
-      const uint32_t s = first ? W[Q + 1] : ext_word(a, e);
-      const uint32_t plus = __popc(~s & mask);
+      const uint32_t sw = first ? W[Q + 1] : ext_word(a, e);
+      const uint32_t plus = __popc(~sw & mask);
       out[1] += plus;
       out[2] += c - plus;
     } else {
@@ -132,6 +156,54 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* sTo, 
     moving -= c;
     first = false;
   }
+}
+
+// The collision of one node, fast path: every occupation <= 64, at most 64
+// removed and at most 32 moving particles, so no extension word is needed, and
+// both probabilities drawn through their tables (0 < P < 2^32).  Returns false
+// (out undefined) when the node falls outside that domain; the caller then runs
+// collide().  Same result as collide() wherever it returns true.
+template <int Q>
+__device__ __forceinline__ bool collide_try_fast(const StepArgs& a, const uint32_t* s, uint32_t node,
+                                                 uint32_t t, const uint32_t (&m)[Q], uint32_t (&out)[Q]) {
+  const uint2* to = thinning_table(s);
+  const uint2* tr = rest_table(s);
+  if (a.omega_mode != kTable || a.rest_mode != kTable) return false;
+  uint32_t mmax = m[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) mmax = max(mmax, m[i]);
+  if (mmax > kDevNmax) return false;
+  const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
+  const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
+  // slot words: thinning 0..Q-1, rest Q, moving Q+1 (and Q+2)
+  const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  uint32_t r[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) r[i] = binomial_alias(to, m[i], W[i]);
+  uint32_t removed = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) removed += r[i];
+  if (removed > kDevNmax) return false;
+  const uint32_t to_rest = binomial_alias(tr, removed, W[Q]);
+  const uint32_t moving = removed - to_rest;
+  if (moving > 32) return false;
+  const uint32_t mask = moving == 32 ? 0xFFFFFFFFu : ((1u << moving) - 1u);
+  out[0] = m[0] - r[0] + to_rest;
+  if constexpr (Q == 3) {
+    const uint32_t minus = __popc(W[Q + 1] & mask);
+    out[1] = m[1] - r[1] + (moving - minus);
+    out[2] = m[2] - r[2] + minus;
+  } else {
+    const uint32_t ax = W[Q + 1] & mask, sg = W[Q + 2] & mask;
+    const uint32_t ny = __popc(ax);          // to +y or -y
+    const uint32_t nmy = __popc(ax & sg);    // to -y
+    const uint32_t nmx = __popc(sg & ~ax);   // to -x
+    out[1] = m[1] - r[1] + (moving - ny - nmx);
+    out[2] = m[2] - r[2] + nmx;
+    out[3] = m[3] - r[3] + (ny - nmy);
+    out[4] = m[4] - r[4] + nmy;
+  }
+  return true;
 }
 
 }  // namespace ilg

@@ -19,7 +19,16 @@ constexpr uint32_t kTagStep = 1;
 constexpr uint32_t kTagExt = 2;
 constexpr uint32_t kTagInit = 3;
 
+constexpr uint32_t kAliasEntries = (kNmax + 1) * (kNmax + 2) / 2;  // rows n = 0..64
+struct AliasEntry {
+  uint32_t thr;    // draws below the threshold keep the column's own outcome
+  uint32_t alias;  // outcome of the other draws of the column
+};
+// device table block: alias(thinning) | alias(rest), AliasEntry each
+constexpr uint32_t kBlockWords = 2 * kAliasEntries * 2;
+
 void build_binomial_table(uint64_t P, uint32_t* T);
+void build_alias_table(uint64_t P, AliasEntry* out);
 uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap);
 uint64_t quantise_probability(double p);
 void weights(int lattice, double theta, double* w);

@@ -11,20 +11,20 @@ namespace ilg {
 // --------------------------------------------------------------------------
 // step: one thread per node, any extent.  Loads the Q occupations of its node,
 // flips, collides and scatters n'_i to the neighbour x + v_i (periodic).
-// The integer tables are staged in shared memory once per block.  A block
-// returns without work when an earlier launch recorded an overflow.
+// The table block (CDF rows and guide cells) is staged in shared memory once per
+// block.  A block returns without work when an earlier launch recorded an
+// overflow.
 // --------------------------------------------------------------------------
 template <int Q>
-__global__ void __launch_bounds__(256) step_generic_kernel(StepArgs a, const uint16_t* __restrict__ in,
-                                                           uint16_t* __restrict__ out, uint32_t t,
-                                                           unsigned long long* __restrict__ fail) {
-  __shared__ uint32_t sT[2 * kDevTableWords];
+__global__ void __launch_bounds__(256, 4) step_kernel(StepArgs a, const uint16_t* __restrict__ in,
+                                                      uint16_t* __restrict__ out, uint32_t t,
+                                                      unsigned long long* __restrict__ fail) {
+  extern __shared__ uint4 smem4[];
   __shared__ int skip;
+  uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
   if (threadIdx.x == 0) skip = (*reinterpret_cast<volatile unsigned long long*>(fail) != ~0ull);
-  for (uint32_t i = threadIdx.x; i < kDevTableWords; i += blockDim.x) {
-    sT[i] = a.T_omega[i];
-    sT[kDevTableWords + i] = a.T_rest[i];
-  }
+  const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
+  for (uint32_t i = threadIdx.x; i < kDevBlockWords / 4; i += blockDim.x) smem4[i] = g4[i];
   __syncthreads();
   if (skip) return;
 
@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(256) step_generic_kernel(StepArgs a, const uin
       m[3] = a.flip ? n[4] : n[3];
       m[4] = a.flip ? n[3] : n[4];
     }
-    collide<Q>(a, sT, sT + kDevTableWords, node, t, m, post);
+    if (!collide_try_fast<Q>(a, s, node, t, m, post))
+      collide<Q>(a, s, node, t, m, post);
 #pragma unroll
     for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
     const uint32_t xp = x + 1 == a.Lx ? 0 : x + 1;
@@ -68,10 +69,18 @@ __global__ void __launch_bounds__(256) step_generic_kernel(StepArgs a, const uin
   if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
 }
 
-cudaError_t launch_step_generic(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out,
-                                uint32_t t, unsigned long long* fail, int grid, cudaStream_t s) {
-  if (Q == 3) step_generic_kernel<3><<<grid, 256, 0, s>>>(a, in, out, t, fail);
-  else step_generic_kernel<5><<<grid, 256, 0, s>>>(a, in, out, t, fail);
+constexpr size_t kStepSmem = sizeof(uint32_t) * kDevBlockWords;
+
+cudaError_t prepare_step_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(step_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStepSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(step_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStepSmem));
+}
+
+cudaError_t launch_step(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
+                        unsigned long long* fail, int grid, cudaStream_t s) {
+  if (Q == 3) step_kernel<3><<<grid, 256, kStepSmem, s>>>(a, in, out, t, fail);
+  else step_kernel<5><<<grid, 256, kStepSmem, s>>>(a, in, out, t, fail);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,277 @@
+// Row-tiled fused step for rows whose length is a multiple of the vector width.
+//
+// A block walks whole rows (grid-stride over y).  Each row is cut into tiles of
+// blockDim vectors; a thread owns one vector of NPT consecutive nodes and moves
+// every plane with one NPT*2-byte load and one store.  The rest plane and the
+// +-y planes are stored straight back (a +-y shift only changes the row).  The
+// +-x planes shift by one node inside the vector: the missing edge value comes
+// from the neighbouring thread through shared memory, from the previous tile
+// (carried), or — at the two ends of a row, where the lattice wraps — from the
+// other end of the same row, so the vectors of the first and last thread are
+// held back until that value exists.  Exchange slots are double-buffered by tile
+// parity, so one barrier per tile suffices.
+#include <cuda_runtime.h>
+
+#include "ilg_device.cuh"
+#include "ilg_launch.h"
+
+namespace ilg {
+
+template <int NPT>
+struct Vec {
+  uint32_t w[NPT / 2];
+};
+
+template <int NPT>
+__device__ __forceinline__ Vec<NPT> vload(const uint16_t* p) {
+  Vec<NPT> v;
+  if constexpr (NPT == 8) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+    v.w[0] = q.x; v.w[1] = q.y; v.w[2] = q.z; v.w[3] = q.w;
+  } else {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    v.w[0] = q.x; v.w[1] = q.y;
+  }
+  return v;
+}
+
+template <int NPT>
+__device__ __forceinline__ void vstore(uint16_t* p, const Vec<NPT>& v) {
+  if constexpr (NPT == 8) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(v.w[0], v.w[1], v.w[2], v.w[3]);
+  } else {
+    *reinterpret_cast<uint2*>(p) = make_uint2(v.w[0], v.w[1]);
+  }
+}
+
+__device__ __forceinline__ uint32_t half(const uint32_t* w, int k) {
+  return (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+}
+
+// +x output: [left, p0 .. p_{NPT-2}]
+template <int NPT>
+__device__ __forceinline__ Vec<NPT> shift_up(const Vec<NPT>& p, uint32_t left) {
+  Vec<NPT> o;
+  o.w[0] = __byte_perm(left, p.w[0], 0x5410);
+#pragma unroll
+  for (int j = 1; j < NPT / 2; ++j) o.w[j] = __byte_perm(p.w[j - 1], p.w[j], 0x5432);
+  return o;
+}
+
+// -x output: [p1 .. p_{NPT-1}, right]
+template <int NPT>
+__device__ __forceinline__ Vec<NPT> shift_down(const Vec<NPT>& p, uint32_t right) {
+  Vec<NPT> o;
+#pragma unroll
+  for (int j = 0; j < NPT / 2 - 1; ++j) o.w[j] = __byte_perm(p.w[j], p.w[j + 1], 0x5432);
+  o.w[NPT / 2 - 1] = __byte_perm(p.w[NPT / 2 - 1], right, 0x5432);
+  return o;
+}
+
+constexpr int kVecThreads = 256;
+
+template <int Q>
+__device__ __forceinline__ void flip(const StepArgs& a, const uint32_t (&n)[Q], uint32_t (&m)[Q]) {
+  m[0] = n[0];
+  m[1] = a.flip ? n[2] : n[1];
+  m[2] = a.flip ? n[1] : n[2];
+  if constexpr (Q == 5) {
+    m[3] = a.flip ? n[4] : n[3];
+    m[4] = a.flip ? n[3] : n[4];
+  }
+}
+
+// the fast-path collision the row-tiled kernel uses
+struct FastCollide {
+  static constexpr uint32_t kSmemWords = kDevBlockWords;  // table block staged in shared memory
+  template <int Q>
+  __device__ __forceinline__ static bool run(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
+                                             const uint32_t (&m)[Q], uint32_t (&post)[Q]) {
+    return collide_try_fast<Q>(a, s, node, t, m, post);
+  }
+};
+
+// flip and collide one node on the fast path (occupations n, result post masked to
+// 16 bits); sets bad when some occupation exceeds 65535; returns false when the
+// node needs the general collision (post is then 0)
+template <int Q, class Coll>
+__device__ __forceinline__ bool node_update(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
+                                            const uint32_t (&n)[Q], uint32_t (&post)[Q], bool& bad) {
+  uint32_t m[Q];
+  flip<Q>(a, n, m);
+  const bool ok = Coll::template run<Q>(a, s, node, t, m, post);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    bad |= ok && post[i] > 65535u;
+    post[i] = ok ? (post[i] & 0xFFFFu) : 0u;
+  }
+  return ok;
+}
+
+template <int Q, int NPT, bool UNROLL, int MINB, class Coll = FastCollide>
+__global__ void __launch_bounds__(kVecThreads, MINB)
+    step_vec_kernel(StepArgs a, const uint16_t* __restrict__ in, uint16_t* __restrict__ out, uint32_t t,
+                    unsigned long long* __restrict__ fail) {
+  extern __shared__ uint4 smem4[];
+  __shared__ uint32_t xs1[2][kVecThreads];  // +x value of each thread's last node
+  __shared__ uint32_t xs2[2][kVecThreads];  // -x value of each thread's first node
+  __shared__ int skip;
+  uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
+  const int tid = threadIdx.x;
+  if (tid == 0) skip = (*reinterpret_cast<volatile unsigned long long*>(fail) != ~0ull);
+  const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
+  for (uint32_t i = tid; i < Coll::kSmemWords / 4; i += blockDim.x) smem4[i] = g4[i];
+  __syncthreads();
+  if (skip) return;
+
+  const uint32_t Lx = a.Lx, Ly = a.Ly;
+  const size_t plane = size_t(Lx) * Ly;
+  const uint32_t vpr = Lx / NPT;                          // vectors per row
+  const uint32_t tiles = (vpr + kVecThreads - 1) / kVecThreads;
+  const int last_tid = int((vpr - 1) % kVecThreads);       // last active thread of a row's last tile
+  bool bad = false;
+  int par = 0;
+
+  for (uint32_t y = blockIdx.x; y < Ly; y += gridDim.x) {
+    const size_t rowoff = size_t(y) * Lx;
+    const uint32_t yp = (Q == 5) ? (y + 1 == Ly ? 0 : y + 1) : 0;
+    const uint32_t ym = (Q == 5) ? (y == 0 ? Ly - 1 : y - 1) : 0;
+    Vec<NPT> held_px;      // thread 0, tile 0: +x vector waiting for the row's last node
+    Vec<NPT> held_mx;      // last thread of a full tile: -x vector waiting for the next tile
+    uint32_t first2 = 0;   // -x value of the row's first node
+    for (uint32_t tile = 0; tile < tiles; ++tile, par ^= 1) {
+      const uint32_t v = tile * kVecThreads + tid;
+      const bool active = v < vpr;
+      const uint32_t x0 = v * NPT;
+      Vec<NPT> P[Q];
+      if (active) {
+        Vec<NPT> N[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) N[i] = vload<NPT>(in + i * plane + rowoff + x0);
+        uint32_t slow = 0;  // nodes that need the general collision
+        if constexpr (UNROLL) {
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            uint32_t n[Q], post[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) n[i] = half(N[i].w, k);
+            if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + k, t, n, post, bad)) slow |= 1u << k;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+              if (k & 1) P[i].w[k >> 1] |= post[i] << 16;
+              else P[i].w[k >> 1] = post[i];
+            }
+          }
+        } else {
+          // rolled over the words: the word in use is always w[0]; inputs move down
+          // one word per pass, finished output words enter at the top
+#pragma unroll 1
+          for (int j = 0; j < NPT / 2; ++j) {
+            uint32_t acc[Q];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              uint32_t n[Q], post[Q];
+#pragma unroll
+              for (int i = 0; i < Q; ++i) n[i] = h ? (N[i].w[0] >> 16) : (N[i].w[0] & 0xFFFFu);
+              if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + 2 * j + h, t, n, post, bad))
+                slow |= 1u << (2 * j + h);
+#pragma unroll
+              for (int i = 0; i < Q; ++i) acc[i] = h ? (acc[i] | (post[i] << 16)) : post[i];
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+#pragma unroll
+              for (int q = 0; q < NPT / 2 - 1; ++q) {
+                N[i].w[q] = N[i].w[q + 1];
+                P[i].w[q] = P[i].w[q + 1];
+              }
+              P[i].w[NPT / 2 - 1] = acc[i];
+            }
+          }
+        }
+        // rare: nodes with an occupation above 64, more than 64 removed or more than
+        // 32 moving particles take the general collision (extension words)
+        while (slow) {
+          const int k = __ffs(slow) - 1;
+          slow &= slow - 1;
+          const size_t at = rowoff + x0 + k;
+          uint32_t n[Q], m[Q], post[Q];
+#pragma unroll
+          for (int i = 0; i < Q; ++i) n[i] = in[i * plane + at];
+          flip<Q>(a, n, m);
+          collide<Q>(a, s, uint32_t(at), t, m, post);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            bad |= post[i] > 65535u;
+            const uint32_t v = post[i] & 0xFFFFu;
+#pragma unroll
+            for (int kk = 0; kk < NPT; ++kk)
+              if (kk == k) P[i].w[kk >> 1] |= v << (16 * (kk & 1));
+          }
+        }
+        vstore<NPT>(out + rowoff + x0, P[0]);
+        if constexpr (Q == 5) {
+          vstore<NPT>(out + 3 * plane + size_t(yp) * Lx + x0, P[3]);
+          vstore<NPT>(out + 4 * plane + size_t(ym) * Lx + x0, P[4]);
+        }
+        xs1[par][tid] = half(P[1].w, NPT - 1);
+        xs2[par][tid] = half(P[2].w, 0);
+      }
+      __syncthreads();
+      if (tile == 0) first2 = xs2[par][0];
+      const bool last_tile = tile + 1 == tiles;
+      // the -x vector held by the previous tile's last thread gets this tile's first node
+      if (tile > 0 && tid == kVecThreads - 1) {
+        const size_t xprev = size_t(tile - 1) * kVecThreads * NPT + size_t(kVecThreads - 1) * NPT;
+        vstore<NPT>(out + 2 * plane + rowoff + xprev, shift_down<NPT>(held_mx, xs2[par][0]));
+      }
+      if (active) {
+        // +x plane
+        if (tid > 0) {
+          vstore<NPT>(out + plane + rowoff + x0, shift_up<NPT>(P[1], xs1[par][tid - 1]));
+        } else if (tile > 0) {
+          vstore<NPT>(out + plane + rowoff + x0, shift_up<NPT>(P[1], xs1[par ^ 1][kVecThreads - 1]));
+        } else {
+          held_px = P[1];
+        }
+        // -x plane
+        if (last_tile && tid == last_tid) {
+          const uint32_t right = (tiles == 1 && tid == 0) ? xs2[par][0] : first2;
+          vstore<NPT>(out + 2 * plane + rowoff + x0, shift_down<NPT>(P[2], right));
+        } else if (tid < kVecThreads - 1) {
+          vstore<NPT>(out + 2 * plane + rowoff + x0, shift_down<NPT>(P[2], xs2[par][tid + 1]));
+        } else {
+          held_mx = P[2];
+        }
+      }
+      if (last_tile && tid == 0) {
+        // the row's first +x vector gets the row's last node
+        vstore<NPT>(out + plane + rowoff, shift_up<NPT>(held_px, xs1[par][last_tid]));
+      }
+    }
+  }
+  if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
+}
+
+constexpr size_t kVecSmem = sizeof(uint32_t) * kDevBlockWords;
+constexpr int kNPT = 8;
+constexpr bool kUnroll = true;
+constexpr int kMinBlocks = 3;
+
+cudaError_t prepare_step_vec_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(step_vec_kernel<3, kNPT, kUnroll, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(kVecSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(step_vec_kernel<5, kNPT, kUnroll, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kVecSmem));
+}
+
+uint32_t step_vec_width() { return kNPT; }
+
+cudaError_t launch_step_vec(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
+                            unsigned long long* fail, int grid, cudaStream_t s) {
+  if (Q == 3) step_vec_kernel<3, kNPT, kUnroll, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+  else step_vec_kernel<5, kNPT, kUnroll, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+  return cudaGetLastError();
+}
+
+}  // namespace ilg

@@ -39,6 +39,51 @@ void build_binomial_table(uint64_t P, uint32_t* T) {
   }
 }
 
+// Alias tables (Walker; Vose's construction carried out in integers) realising
+// the integer pmf of each CDF row exactly.  Row n (0..kNmax) has n+1 columns at
+// entry offset n(n+1)/2; column j owns the draws u with floor(u (n+1) / 2^32) = j,
+// i.e. [ceil(j 2^32/(n+1)), ceil((j+1) 2^32/(n+1))).  The draw yields j when u is
+// below the column's threshold, its alias otherwise.
+void build_alias_table(uint64_t P, AliasEntry* out) {
+  std::vector<uint32_t> cdf(kTableWords);
+  build_binomial_table(P, cdf.data());
+  std::vector<uint64_t> weight(kNmax + 1), start(kNmax + 2);
+  std::vector<uint32_t> under, over;
+  for (uint32_t n = 0; n <= kNmax; ++n) {
+    AliasEntry* row = out + n * (n + 1) / 2;
+    uint64_t below = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+      const uint64_t c = cdf[n * (n - 1) / 2 + k];
+      weight[k] = c - below;
+      below = c;
+    }
+    weight[n] = (uint64_t(1) << 32) - below;
+    for (uint32_t j = 0; j <= n + 1; ++j) start[j] = ((uint64_t(j) << 32) + n) / (n + 1);
+    under.clear();
+    over.clear();
+    for (uint32_t j = 0; j <= n; ++j) {
+      row[j].thr = 0;
+      row[j].alias = j;
+      const uint64_t size = start[j + 1] - start[j];
+      if (weight[j] < size) under.push_back(j);
+      else if (weight[j] > size) over.push_back(j);
+    }
+    while (!under.empty() && !over.empty()) {
+      const uint32_t l = under.back();
+      under.pop_back();
+      const uint32_t g = over.back();
+      over.pop_back();
+      const uint64_t lsize = start[l + 1] - start[l];
+      row[l].thr = uint32_t(start[l] + weight[l]);
+      row[l].alias = g;
+      weight[g] -= lsize - weight[l];
+      const uint64_t gsize = start[g + 1] - start[g];
+      if (weight[g] < gsize) under.push_back(g);
+      else if (weight[g] > gsize) over.push_back(g);
+    }
+  }
+}
+
 // Poisson(lambda) CDF scaled to 2^32, floored, saturating at 2^32 - 1, up to and
 // including the first saturated entry.  Returns the entry count, 0 if above cap.
 uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap) {

@@ -49,6 +49,9 @@ def test_philox_device_matches_oracle(B):
 def test_binomial_tables_match(B, p):
     P = O.quantise(p)
     assert np.array_equal(B.binomial_table(P), O.binomial_table(P))
+    thr, al = B.alias_table(P)
+    othr, oal = O.alias_table(P)
+    assert np.array_equal(thr, othr) and np.array_equal(al, oal.astype(np.uint32))
 
 
 @pytest.mark.parametrize("lam", [0.0, 1e-3, 0.5, 10.0, 30.0, 50.0 + 4.0 * 0.7071067811865476, 200.0, 699.0])
@@ -90,6 +93,12 @@ STEP_CASES = [
     (2, 33, 17, 1.9, 0.5, 12.0, 0),
     (2, 16, 16, 1e-12, 1.0 / 3.0, 8.0, 0),
     (2, 24, 40, 1.3, 0.45, 60.0, 40),
+    # row-tiled kernel: rows of 1, 2 and 3 tiles with ragged last tiles, one-vector rows
+    (2, 2344, 5, 1.8, 1.0 / 3.0, 10.0, 30),
+    (1, 4104, 1, 1.4, 1.0 / 3.0, 70.0, 12),
+    (2, 8, 6, 1.6, 1.0 / 3.0, 20.0, 0),
+    (1, 8, 1, 0.9, 1.0 / 3.0, 40.0, 0),
+    (2, 2048, 3, 0.7, 1.0 / 3.0, 30.0, 0),
 ]
 
 

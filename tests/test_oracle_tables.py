@@ -85,3 +85,39 @@ def test_poisson_table_exact(lam):
     acc += term
     tail = 1 - acc
     assert tail < mpmath.mpf(2) ** -31
+
+
+def alias_induced_weights(thr, al, n):
+    """Exact number of 32-bit draws u that the alias row n maps to each outcome:
+    column j = floor(u (n+1) / 2^32) covers [a_j, a_{j+1}), a_j = ceil(j 2^32 / (n+1));
+    u < thr[j] gives j, else alias[j]."""
+    off = n * (n + 1) // 2
+    cnt = [0] * (n + 1)
+    for j in range(n + 1):
+        a0 = -((-(j << 32)) // (n + 1))
+        a1 = -((-((j + 1) << 32)) // (n + 1))
+        t = int(thr[off + j])
+        alias = int(al[off + j])
+        if alias == j:
+            cnt[j] += a1 - a0
+        else:
+            assert a0 <= t <= a1
+            cnt[j] += t - a0
+            cnt[alias] += a1 - t
+    return cnt
+
+
+@pytest.mark.parametrize("p", [1e-9, 0.2, 1.0 / 3.0, 0.5, 0.9, 0.999])
+def test_alias_table_realises_pmf_exactly(p):
+    """Every draw u in [0, 2^32) is accounted for, and each outcome k of row n gets
+    exactly W_k = T[n][k] - T[n][k-1] draws (the integer pmf of the CDF table)."""
+    P = O.quantise(p)
+    T = O.binomial_table(P).astype(np.int64)
+    thr, al = O.alias_table(P)
+    for n in range(0, O.NMAX + 1):
+        if n == 0:
+            W = [1 << 32]
+        else:
+            row = [int(v) for v in T[n * (n - 1) // 2: n * (n - 1) // 2 + n]]
+            W = [row[0]] + [row[k] - row[k - 1] for k in range(1, n)] + [(1 << 32) - row[-1]]
+        assert alias_induced_weights(thr, al, n) == W, (p, n)
