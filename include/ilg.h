@@ -125,6 +125,29 @@ ilg_status ilg_observables(ilg_ctx* ctx, const int32_t* modes, uint32_t nmodes, 
                            uint64_t* mass, double* re, double* im, double* amp, double* Sk,
                            int64_t* col_sums, int64_t* row_sums);
 
+/* Observables of a state in caller-owned device memory, allocating nothing (the
+ * paper has no counterpart; this serves callers that cannot allocate device memory
+ * when they need the numbers: code running while a stream is captured into a CUDA
+ * graph, real-time loops that must not take the allocator's locks or its implicit
+ * synchronisation, hosts whose device memory all belongs to their own pool).
+ *   lattice, Lx, Ly  as in ilg_params (Ly taken as 1 for D1Q3); Lx, Ly <= 32768
+ *   state            device array, Q*Lx*Ly uint16 in the plane layout above (read only)
+ *   modes, nmodes    host array of nmodes <= 256 axis modes (mx, my), as ilg_observables
+ *   stream           cudaStream_t the work runs on
+ *   mass, re, im, amp, Sk   host outputs as in ilg_observables (each may be NULL)
+ * The results equal those of ilg_observables on the same state.  Scratch lives in a
+ * static device array of about 530 KB that every GPU which loads the library holds
+ * until the process exits; nothing is allocated or freed.  The first call on a device
+ * looks up that array's device address (with the device current) and caches it:
+ * make that first call before any stream capture.  All calls share the one array and
+ * each clears the sums it accumulates: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.  Sizes
+ * beyond the limits give ILG_E_INVALID (message in ilg_last_error(NULL)).
+ * Synchronous: returns after the results are on the host. */
+ilg_status ilg_observables_noalloc(int32_t lattice, uint32_t Lx, uint32_t Ly, const uint16_t* state,
+                                   const int32_t* modes, uint32_t nmodes, void* stream, uint64_t* mass,
+                                   double* re, double* im, double* amp, double* Sk);
+
 /* Diagnostics of the building blocks, for parity tests.
  * ilg_philox: n Philox4x32-10 blocks computed on the device; ctr (4n words) and out
  *   (4n words) are host arrays; key = (seed lo32, seed hi32).

@@ -61,13 +61,16 @@ _lib.ilg_get_state_device.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(
 _lib.ilg_step.argtypes = [_vp, ctypes.c_uint32]
 _lib.ilg_observables.argtypes = [_vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(ctypes.c_uint64), _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.ilg_observables_noalloc.argtypes = [ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp,
+                                         ctypes.c_uint32, _vp, ctypes.POINTER(ctypes.c_uint64), _vp, _vp, _vp,
+                                         _vp]
 _lib.ilg_philox.argtypes = [_u32p, ctypes.c_uint64, _u32p, ctypes.c_size_t, _vp]
 _lib.ilg_binomial_table.argtypes = [ctypes.c_uint64, _u32p]
 _lib.ilg_alias_table.argtypes = [ctypes.c_uint64, _u32p, _u32p]
 _lib.ilg_poisson_table.argtypes = [ctypes.c_double, _u32p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
 for _f in ("ilg_create", "ilg_destroy", "ilg_init", "ilg_set_state", "ilg_set_state_device", "ilg_get_state",
            "ilg_get_state_device", "ilg_step", "ilg_observables", "ilg_philox", "ilg_binomial_table",
-           "ilg_alias_table", "ilg_poisson_table"):
+           "ilg_alias_table", "ilg_poisson_table", "ilg_observables_noalloc"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -175,6 +178,19 @@ class Lattice:
                                     col.ctypes.data if col is not None else None,
                                     row.ctypes.data if row is not None else None), self._h)
         return dict(t=int(t.value), mass=int(M.value), re=re, im=im, amp=amp, Sk=Sk, col=col, row=row)
+
+
+def observables_noalloc(lattice: int, Lx: int, Ly: int, state_dev_ptr: int, modes=(), stream=None):
+    """ilg_observables_noalloc on a device state (see include/ilg.h)."""
+    modes = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, 2))
+    n = len(modes)
+    re, im, amp, Sk = (np.zeros(n) for _ in range(4))
+    M = ctypes.c_uint64()
+    _check(_lib.ilg_observables_noalloc(int(lattice), int(Lx), int(Ly), _vp(state_dev_ptr),
+                                        modes.ctypes.data if n else None, n, _vp(stream_handle(stream)),
+                                        ctypes.byref(M), re.ctypes.data, im.ctypes.data, amp.ctypes.data,
+                                        Sk.ctypes.data))
+    return dict(mass=int(M.value), re=re, im=im, amp=amp, Sk=Sk)
 
 
 def philox(ctr: np.ndarray, seed: int, stream=None) -> np.ndarray:

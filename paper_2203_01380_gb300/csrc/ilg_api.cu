@@ -133,6 +133,11 @@ void free_ctx(ilg_ctx* c) {
 
 }  // namespace
 
+namespace ilg {
+// message for ilg_last_error(NULL), set by entry points that have no context
+void set_context_free_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace ilg
+
 extern "C" {
 
 const char* ilg_last_error(const ilg_ctx* ctx) {

@@ -43,4 +43,6 @@ struct InitTables {
 };
 bool build_init_tables(const ilg_params& p, int Q, InitTables* out, std::string* err);
 
+void set_context_free_error(const std::string& msg);
+
 }  // namespace ilg
