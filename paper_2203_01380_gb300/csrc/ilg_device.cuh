@@ -158,21 +158,22 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* s, ui
   }
 }
 
-// The collision of one node, fast path: every occupation <= 64, at most 64
+// The collision of one node, fast path: every occupation <= 63, at most 63
 // removed and at most 32 moving particles, so no extension word is needed, and
 // both probabilities drawn through their tables (0 < P < 2^32).  Returns false
 // (out undefined) when the node falls outside that domain; the caller then runs
-// collide().  Same result as collide() wherever it returns true.
+// collide().  Same result as collide() wherever it returns true.  No result can
+// exceed 65535 here (mass is conserved and at most 5 * 63).
 template <int Q>
 __device__ __forceinline__ bool collide_try_fast(const StepArgs& a, const uint32_t* s, uint32_t node,
                                                  uint32_t t, const uint32_t (&m)[Q], uint32_t (&out)[Q]) {
   const uint2* to = thinning_table(s);
   const uint2* tr = rest_table(s);
   if (a.omega_mode != kTable || a.rest_mode != kTable) return false;
-  uint32_t mmax = m[0];
+  uint32_t any = m[0];
 #pragma unroll
-  for (int i = 1; i < Q; ++i) mmax = max(mmax, m[i]);
-  if (mmax > kDevNmax) return false;
+  for (int i = 1; i < Q; ++i) any |= m[i];
+  if (any >> 6) return false;
   const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
   const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
   // slot words: thinning 0..Q-1, rest Q, moving Q+1 (and Q+2)
@@ -183,7 +184,7 @@ __device__ __forceinline__ bool collide_try_fast(const StepArgs& a, const uint32
   uint32_t removed = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) removed += r[i];
-  if (removed > kDevNmax) return false;
+  if (removed >> 6) return false;
   const uint32_t to_rest = binomial_alias(tr, removed, W[Q]);
   const uint32_t moving = removed - to_rest;
   if (moving > 32) return false;

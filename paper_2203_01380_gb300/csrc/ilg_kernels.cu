@@ -49,10 +49,11 @@ __global__ void __launch_bounds__(256, 4) step_kernel(StepArgs a, const uint16_t
       m[3] = a.flip ? n[4] : n[3];
       m[4] = a.flip ? n[3] : n[4];
     }
-    if (!collide_try_fast<Q>(a, s, node, t, m, post))
+    if (!collide_try_fast<Q>(a, s, node, t, m, post)) {
       collide<Q>(a, s, node, t, m, post);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
+      for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
+    }
     const uint32_t xp = x + 1 == a.Lx ? 0 : x + 1;
     const uint32_t xm = x == 0 ? a.Lx - 1 : x - 1;
     const size_t row = size_t(y) * a.Lx;

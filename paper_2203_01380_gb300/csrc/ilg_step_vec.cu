@@ -28,9 +28,11 @@ __device__ __forceinline__ Vec<NPT> vload(const uint16_t* p) {
   if constexpr (NPT == 8) {
     const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
     v.w[0] = q.x; v.w[1] = q.y; v.w[2] = q.z; v.w[3] = q.w;
-  } else {
+  } else if constexpr (NPT == 4) {
     const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
     v.w[0] = q.x; v.w[1] = q.y;
+  } else {
+    v.w[0] = __ldg(reinterpret_cast<const uint32_t*>(p));
   }
   return v;
 }
@@ -39,8 +41,10 @@ template <int NPT>
 __device__ __forceinline__ void vstore(uint16_t* p, const Vec<NPT>& v) {
   if constexpr (NPT == 8) {
     *reinterpret_cast<uint4*>(p) = make_uint4(v.w[0], v.w[1], v.w[2], v.w[3]);
-  } else {
+  } else if constexpr (NPT == 4) {
     *reinterpret_cast<uint2*>(p) = make_uint2(v.w[0], v.w[1]);
+  } else {
+    *reinterpret_cast<uint32_t*>(p) = v.w[0];
   }
 }
 
@@ -91,27 +95,24 @@ struct FastCollide {
   }
 };
 
-// flip and collide one node on the fast path (occupations n, result post masked to
-// 16 bits); sets bad when some occupation exceeds 65535; returns false when the
-// node needs the general collision (post is then 0)
+// flip and collide one node on the fast path (no result there exceeds 65535);
+// returns false when the node needs the general collision (post is then 0)
 template <int Q, class Coll>
 __device__ __forceinline__ bool node_update(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
-                                            const uint32_t (&n)[Q], uint32_t (&post)[Q], bool& bad) {
+                                            const uint32_t (&n)[Q], uint32_t (&post)[Q]) {
   uint32_t m[Q];
   flip<Q>(a, n, m);
   const bool ok = Coll::template run<Q>(a, s, node, t, m, post);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    bad |= ok && post[i] > 65535u;
-    post[i] = ok ? (post[i] & 0xFFFFu) : 0u;
-  }
+  for (int i = 0; i < Q; ++i) post[i] = ok ? post[i] : 0u;
   return ok;
 }
 
-template <int Q, int NPT, bool UNROLL, int MINB, class Coll = FastCollide>
-__global__ void __launch_bounds__(kVecThreads, MINB)
+template <int Q, int NPT, bool UNROLL, int MINB, class Coll = FastCollide, int THREADS = kVecThreads>
+__global__ void __launch_bounds__(THREADS, MINB)
     step_vec_kernel(StepArgs a, const uint16_t* __restrict__ in, uint16_t* __restrict__ out, uint32_t t,
                     unsigned long long* __restrict__ fail) {
+  constexpr int kVecThreads = THREADS;
   extern __shared__ uint4 smem4[];
   __shared__ uint32_t xs1[2][kVecThreads];  // +x value of each thread's last node
   __shared__ uint32_t xs2[2][kVecThreads];  // -x value of each thread's first node
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kVecThreads, MINB)
             uint32_t n[Q], post[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) n[i] = half(N[i].w, k);
-            if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + k, t, n, post, bad)) slow |= 1u << k;
+            if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + k, t, n, post)) slow |= 1u << k;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
               if (k & 1) P[i].w[k >> 1] |= post[i] << 16;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kVecThreads, MINB)
               uint32_t n[Q], post[Q];
 #pragma unroll
               for (int i = 0; i < Q; ++i) n[i] = h ? (N[i].w[0] >> 16) : (N[i].w[0] & 0xFFFFu);
-              if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + 2 * j + h, t, n, post, bad))
+              if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + 2 * j + h, t, n, post))
                 slow |= 1u << (2 * j + h);
 #pragma unroll
               for (int i = 0; i < Q; ++i) acc[i] = h ? (acc[i] | (post[i] << 16)) : post[i];
