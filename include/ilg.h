@@ -125,6 +125,35 @@ ilg_status ilg_observables(ilg_ctx* ctx, const int32_t* modes, uint32_t nmodes, 
                            uint64_t* mass, double* re, double* im, double* amp, double* Sk,
                            int64_t* col_sums, int64_t* row_sums);
 
+/* ---------------------------------------------------------------------------
+ * Batched D1Q3 replicas (independent rings of differing length, occupation and
+ * omega_eff, as the ensembles of Sec. V).  One persistent kernel launch, captured
+ * in a CUDA graph, advances every ring: blocks take rings longest first, hold a
+ * ring and its alias tables in shared memory for all steps, and write it back.
+ * Results equal, bit for bit, those of one context per ring (ilg_create ...), as
+ * every random number is keyed by the ring's replica word.  All rings of a batch
+ * share one seed; Lx <= 16384 each.  Host arrays only; calls synchronise.
+ *   ilg_batch_create   params: n D1Q3 parameter sets (replica i = params[i]); tables
+ *                      and device memory for all rings (stream NULL: a private one)
+ *   ilg_batch_init     Poisson initial state of every ring (as ilg_init), t := 0
+ *   ilg_batch_set_state / get_state   ring i, 3*Lx uint16 (planes rest, +1, -1)
+ *   ilg_batch_run      T steps for every ring; if amp_record != NULL it receives
+ *                      n*T doubles, A^LG of mode record_mode of ring i after step s
+ *                      at [i*T + s] (as ilg_observables' amp).  ILG_E_OVERFLOW: some
+ *                      ring stopped at the step that would exceed 65535 (its state
+ *                      and t are those before that step); the others completed
+ *   ilg_batch_observables   per ring: mass[i] and A^LG of one mode amp[i]
+ * --------------------------------------------------------------------------- */
+typedef struct ilg_batch ilg_batch;
+ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, ilg_batch** out);
+ilg_status ilg_batch_destroy(ilg_batch* b);
+const char* ilg_batch_last_error(const ilg_batch* b);
+ilg_status ilg_batch_init(ilg_batch* b);
+ilg_status ilg_batch_set_state(ilg_batch* b, uint32_t i, const uint16_t* host, size_t n, uint64_t t);
+ilg_status ilg_batch_get_state(ilg_batch* b, uint32_t i, uint16_t* host, size_t n, uint64_t* t);
+ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record);
+ilg_status ilg_batch_observables(ilg_batch* b, int32_t mode, uint64_t* mass, double* amp);
+
 /* Observables of a state in caller-owned device memory, allocating nothing (the
  * paper has no counterpart; this serves callers that cannot allocate device memory
  * when they need the numbers: code running while a stream is captured into a CUDA

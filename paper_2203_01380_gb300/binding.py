@@ -64,13 +64,23 @@ _lib.ilg_observables.argtypes = [_vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctype
 _lib.ilg_observables_noalloc.argtypes = [ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp,
                                          ctypes.c_uint32, _vp, ctypes.POINTER(ctypes.c_uint64), _vp, _vp, _vp,
                                          _vp]
+_lib.ilg_batch_create.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.POINTER(_vp)]
+_lib.ilg_batch_destroy.argtypes = [_vp]
+_lib.ilg_batch_last_error.argtypes = [_vp]
+_lib.ilg_batch_last_error.restype = ctypes.c_char_p
+_lib.ilg_batch_init.argtypes = [_vp]
+_lib.ilg_batch_set_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t, ctypes.c_uint64]
+_lib.ilg_batch_get_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
+_lib.ilg_batch_run.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp]
+_lib.ilg_batch_observables.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
 _lib.ilg_philox.argtypes = [_u32p, ctypes.c_uint64, _u32p, ctypes.c_size_t, _vp]
 _lib.ilg_binomial_table.argtypes = [ctypes.c_uint64, _u32p]
 _lib.ilg_alias_table.argtypes = [ctypes.c_uint64, _u32p, _u32p]
 _lib.ilg_poisson_table.argtypes = [ctypes.c_double, _u32p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
 for _f in ("ilg_create", "ilg_destroy", "ilg_init", "ilg_set_state", "ilg_set_state_device", "ilg_get_state",
            "ilg_get_state_device", "ilg_step", "ilg_observables", "ilg_philox", "ilg_binomial_table",
-           "ilg_alias_table", "ilg_poisson_table", "ilg_observables_noalloc"):
+           "ilg_alias_table", "ilg_poisson_table", "ilg_observables_noalloc", "ilg_batch_create", "ilg_batch_destroy",
+           "ilg_batch_init", "ilg_batch_set_state", "ilg_batch_get_state", "ilg_batch_run", "ilg_batch_observables"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -178,6 +188,66 @@ class Lattice:
                                     col.ctypes.data if col is not None else None,
                                     row.ctypes.data if row is not None else None), self._h)
         return dict(t=int(t.value), mass=int(M.value), re=re, im=im, amp=amp, Sk=Sk, col=col, row=row)
+
+
+class Batch:
+    """Batched D1Q3 rings (ilg_batch_*); replicas: list of parameter dicts."""
+
+    def __init__(self, replicas, stream=None):
+        self.params = (Params * len(replicas))(*[make_params(**r) for r in replicas])
+        self.n = len(replicas)
+        self.L = [int(p.Lx) for p in self.params]
+        h = _vp()
+        st = _lib.ilg_batch_create(self.params, self.n, _vp(stream_handle(stream)), ctypes.byref(h))
+        if st != ILG_OK:
+            raise IlgError(st, _lib.ilg_batch_last_error(None).decode(errors="replace"))
+        self._h = h
+
+    def _check(self, st):
+        if st != ILG_OK:
+            raise IlgError(st, _lib.ilg_batch_last_error(self._h).decode(errors="replace"))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ilg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init(self):
+        self._check(_lib.ilg_batch_init(self._h))
+
+    def set_state(self, i, state, t=0):
+        s = np.ascontiguousarray(state, dtype=np.uint16)
+        self._check(_lib.ilg_batch_set_state(self._h, i, s.ctypes.data, s.size, int(t)))
+
+    def get_state(self, i):
+        out = np.empty((3, 1, self.L[i]), dtype=np.uint16)
+        t = ctypes.c_uint64()
+        self._check(_lib.ilg_batch_get_state(self._h, i, out.ctypes.data, out.size, ctypes.byref(t)))
+        return out, int(t.value)
+
+    def run(self, T, record_mode=None):
+        rec = np.zeros((self.n, T)) if record_mode is not None else None
+        self._check(_lib.ilg_batch_run(self._h, int(T), int(record_mode or 0),
+                                       rec.ctypes.data if rec is not None else None))
+        return rec
+
+    def observables(self, mode=1):
+        mass = np.zeros(self.n, dtype=np.uint64)
+        amp = np.zeros(self.n)
+        self._check(_lib.ilg_batch_observables(self._h, int(mode), mass.ctypes.data, amp.ctypes.data))
+        return mass, amp
 
 
 def observables_noalloc(lattice: int, Lx: int, Ly: int, state_dev_ptr: int, modes=(), stream=None):

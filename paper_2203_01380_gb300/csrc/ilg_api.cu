@@ -67,7 +67,10 @@ uint32_t prob_mode(uint64_t P) {
   return kTable;
 }
 
-std::string validate(const ilg_params& p) {
+}  // namespace
+
+namespace ilg {
+std::string validate_params(const ilg_params& p) {
   if (p.lattice != ILG_D1Q3 && p.lattice != ILG_D2Q5) return "lattice must be ILG_D1Q3 or ILG_D2Q5";
   if (p.reserved != 0) return "reserved field must be 0";
   const uint64_t Ly = p.lattice == ILG_D1Q3 ? 1 : p.Ly;
@@ -83,6 +86,20 @@ std::string validate(const ilg_params& p) {
   if (p.lattice == ILG_D1Q3 && p.mode_my != 0) return "D1Q3 has no y mode";
   return "";
 }
+
+void round_keys(uint64_t seed, uint32_t* rk) {
+  uint32_t k0 = uint32_t(seed), k1 = uint32_t(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = k0;
+    rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+}  // namespace ilg
+
+namespace {
+using ilg::validate_params;
 
 int step_grid(const ilg_ctx* c) {
   const size_t blocks = (c->nodes + 255) / 256;
@@ -108,13 +125,7 @@ StepArgs step_args(const ilg_ctx* c) {
   a.key1 = uint32_t(c->p.seed >> 32);
   a.replica = c->p.replica;
   a.tables = c->d_tables;
-  uint32_t k0 = a.key0, k1 = a.key1;
-  for (int r = 0; r < 10; ++r) {
-    a.rk[2 * r] = k0;
-    a.rk[2 * r + 1] = k1;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
+  ilg::round_keys(c->p.seed, a.rk);
   return a;
 }
 
@@ -148,7 +159,7 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
   if (!out) return fail(nullptr, ILG_E_INVALID, "out is NULL");
   *out = nullptr;
   if (!params) return fail(nullptr, ILG_E_INVALID, "params is NULL");
-  const std::string bad = validate(*params);
+  const std::string bad = validate_params(*params);
   if (!bad.empty()) return fail(nullptr, ILG_E_INVALID, bad);
   ilg_ctx* c = new (std::nothrow) ilg_ctx();
   if (!c) return fail(nullptr, ILG_E_OOM, "host allocation failed");

@@ -1,0 +1,45 @@
+// Batched D1Q3 replicas: device descriptors and the persistent kernel's launcher.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "ilg_device.cuh"
+
+namespace ilg {
+
+constexpr uint32_t kBatchMaxL = 16384;  // longest ring (the ring and its copy live in shared memory)
+
+struct ReplicaDesc {
+  uint32_t L;           // ring length
+  uint32_t flip;
+  uint32_t omega_mode;  // kNever / kTable / kAlways
+  uint32_t rest_mode;
+  uint32_t replica;     // replica word of the Philox counter
+  uint32_t t;           // step counter (advanced by the kernel)
+  uint64_t state_off;   // first of the replica's 3 L occupations in the batch buffer
+};
+
+struct BatchArgs {
+  uint32_t n;              // replicas
+  uint32_t T;              // steps per launch
+  uint32_t Lmax;           // longest ring
+  int32_t record_mode;     // wave number of the recorded amplitude (record != NULL)
+  const uint32_t* order;   // replica ids, longest first
+  ReplicaDesc* desc;
+  const uint32_t* tables;  // kDevBlockWords words per replica
+  uint16_t* state;
+  unsigned int* counter;   // work queue head, 0 at launch
+  uint32_t* failed;        // per replica: 1 when a step would exceed 65535
+  double* record;          // n x T amplitudes A^LG after every step, or NULL
+};
+
+size_t batch_smem_bytes(uint32_t Lmax);
+cudaError_t prepare_batch_kernel(uint32_t Lmax);
+cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int grid, cudaStream_t s);
+cudaError_t launch_batch_obs(const ReplicaDesc* desc, const uint16_t* state, uint32_t n, int32_t mode,
+                             unsigned long long* mass, double* amp, cudaStream_t s);
+
+}  // namespace ilg

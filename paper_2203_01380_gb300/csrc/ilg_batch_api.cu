@@ -1,0 +1,331 @@
+// C ABI of the batched D1Q3 mode (ilg_batch_*): many independent rings advanced
+// together by one persistent kernel launch, captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ilg_batch.h"
+#include "ilg_internal.h"
+#include "ilg_launch.h"
+
+using namespace ilg;
+
+struct ilg_batch {
+  uint32_t n = 0;
+  std::vector<ilg_params> p;
+  std::vector<ReplicaDesc> desc;      // host mirror (t updated after each run)
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;            // created here: a capture needs a non-legacy stream
+  int sms = 0;
+  uint32_t Lmax = 0;
+  size_t total = 0;                   // uint16 words of state
+  uint16_t* d_state = nullptr;
+  ReplicaDesc* d_desc = nullptr;
+  uint32_t* d_tables = nullptr;
+  uint32_t* d_order = nullptr;
+  unsigned int* d_counter = nullptr;
+  uint32_t* d_failed = nullptr;
+  double* d_record = nullptr;
+  size_t record_cap = 0;
+  unsigned long long* d_mass = nullptr;
+  double* d_amp = nullptr;
+  StepArgs common{};
+  cudaGraphExec_t graph = nullptr;
+  uint32_t graph_T = 0;
+  bool graph_rec = false;
+  int32_t graph_mode = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+ilg_status bfail(ilg_batch* b, ilg_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  else g_batch_create_error = msg;
+  return s;
+}
+
+ilg_status bcuda(ilg_batch* b, cudaError_t e, const char* what) {
+  return bfail(b, e == cudaErrorMemoryAllocation ? ILG_E_OOM : ILG_E_CUDA,
+               std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define BCUDA(b, call, what)                           \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return bcuda(b, e_, what);  \
+  } while (0)
+
+uint32_t mode_of(uint64_t P) {
+  if (P == 0) return kNever;
+  if (P == (uint64_t(1) << 32)) return kAlways;
+  return kTable;
+}
+
+void free_batch(ilg_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  cudaFree(b->d_state);
+  cudaFree(b->d_desc);
+  cudaFree(b->d_tables);
+  cudaFree(b->d_order);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_failed);
+  cudaFree(b->d_record);
+  cudaFree(b->d_mass);
+  cudaFree(b->d_amp);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ilg_batch_last_error(const ilg_batch* b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, ilg_batch** out) {
+  if (!out) return bfail(nullptr, ILG_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!params || n == 0) return bfail(nullptr, ILG_E_INVALID, "need at least one replica");
+  for (uint32_t i = 0; i < n; ++i) {
+    const std::string bad = validate_params(params[i]);
+    if (!bad.empty()) return bfail(nullptr, ILG_E_INVALID, "replica " + std::to_string(i) + ": " + bad);
+    if (params[i].lattice != ILG_D1Q3) return bfail(nullptr, ILG_E_INVALID, "batches hold D1Q3 rings");
+    if (params[i].seed != params[0].seed) return bfail(nullptr, ILG_E_INVALID, "all replicas of a batch share one seed");
+    if (params[i].Lx > kBatchMaxL) return bfail(nullptr, ILG_E_INVALID, "ring longer than 16384");
+  }
+  ilg_batch* b = new (std::nothrow) ilg_batch();
+  if (!b) return bfail(nullptr, ILG_E_OOM, "host allocation failed");
+  b->n = n;
+  b->p.assign(params, params + n);
+  b->stream = static_cast<cudaStream_t>(stream);
+  auto bail = [&](cudaError_t e, const char* what) {
+    bcuda(nullptr, e, what);
+    free_batch(b);
+    delete b;
+    return e == cudaErrorMemoryAllocation ? ILG_E_OOM : ILG_E_CUDA;
+  };
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return bail(e, "device query");
+  if (!b->stream) {
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "cudaStreamCreate");
+    b->own_stream = true;
+  }
+  b->desc.resize(n);
+  std::vector<uint32_t> tables(size_t(n) * kBlockWords, 0u);
+  for (uint32_t i = 0; i < n; ++i) {
+    const ilg_params& q = b->p[i];
+    ReplicaDesc& d = b->desc[i];
+    double w[5];
+    weights(ILG_D1Q3, q.theta, w);
+    const double omega_star = q.omega_eff > 1.0 ? 2.0 - q.omega_eff : q.omega_eff;
+    const uint64_t Po = quantise_probability(omega_star), Pr = quantise_probability(w[0]);
+    d.L = q.Lx;
+    d.flip = q.omega_eff > 1.0 ? 1u : 0u;
+    d.omega_mode = mode_of(Po);
+    d.rest_mode = mode_of(Pr);
+    d.replica = q.replica;
+    d.t = 0;
+    d.state_off = b->total;
+    b->total += 3 * size_t(q.Lx);
+    b->Lmax = std::max(b->Lmax, q.Lx);
+    AliasEntry* al = reinterpret_cast<AliasEntry*>(tables.data() + size_t(i) * kBlockWords);
+    if (d.omega_mode == kTable) build_alias_table(Po, al);
+    if (d.rest_mode == kTable) build_alias_table(Pr, al + kAliasEntries);
+  }
+  // longest rings first
+  std::vector<uint32_t> order(n);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return b->desc[x].L > b->desc[y].L; });
+
+  if ((e = cudaMalloc(&b->d_state, sizeof(uint16_t) * b->total)) != cudaSuccess) return bail(e, "cudaMalloc state");
+  if ((e = cudaMalloc(&b->d_desc, sizeof(ReplicaDesc) * n)) != cudaSuccess) return bail(e, "cudaMalloc desc");
+  if ((e = cudaMalloc(&b->d_tables, sizeof(uint32_t) * tables.size())) != cudaSuccess) return bail(e, "cudaMalloc tables");
+  if ((e = cudaMalloc(&b->d_order, sizeof(uint32_t) * n)) != cudaSuccess) return bail(e, "cudaMalloc order");
+  if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned int))) != cudaSuccess) return bail(e, "cudaMalloc counter");
+  if ((e = cudaMalloc(&b->d_failed, sizeof(uint32_t) * n)) != cudaSuccess) return bail(e, "cudaMalloc flags");
+  if ((e = cudaMalloc(&b->d_mass, sizeof(unsigned long long) * n)) != cudaSuccess) return bail(e, "cudaMalloc mass");
+  if ((e = cudaMalloc(&b->d_amp, sizeof(double) * n)) != cudaSuccess) return bail(e, "cudaMalloc amp");
+  if ((e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(ReplicaDesc) * n, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->d_tables, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b->d_state, 0, sizeof(uint16_t) * b->total, b->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+    return bail(e, "upload");
+  if ((e = prepare_batch_kernel(b->Lmax)) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
+  round_keys(params[0].seed, b->common.rk);
+  b->common.key0 = uint32_t(params[0].seed);
+  b->common.key1 = uint32_t(params[0].seed >> 32);
+  *out = b;
+  return ILG_OK;
+}
+
+ilg_status ilg_batch_destroy(ilg_batch* b) {
+  if (!b) return ILG_OK;
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+  delete b;
+  return ILG_OK;
+}
+
+ilg_status ilg_batch_init(ilg_batch* b) {
+  if (!b) return ILG_E_INVALID;
+  // every replica's Poisson tables in one upload, then one init launch per replica
+  std::vector<InitTables> its(b->n);
+  std::vector<uint32_t> all;
+  std::vector<size_t> base(b->n);
+  for (uint32_t i = 0; i < b->n; ++i) {
+    std::string msg;
+    if (!build_init_tables(b->p[i], 3, &its[i], &msg)) return bfail(b, ILG_E_INVALID, "replica " + std::to_string(i) + ": " + msg);
+    base[i] = all.size();
+    all.insert(all.end(), its[i].offset.begin(), its[i].offset.end());
+    all.insert(all.end(), its[i].count.begin(), its[i].count.end());
+    all.insert(all.end(), its[i].table.begin(), its[i].table.end());
+  }
+  uint32_t* d_all = nullptr;
+  BCUDA(b, cudaMalloc(&d_all, sizeof(uint32_t) * all.size()), "cudaMalloc init tables");
+  cudaError_t e = cudaMemcpyAsync(d_all, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice, b->stream);
+  for (uint32_t i = 0; i < b->n && e == cudaSuccess; ++i) {
+    const ilg_params& q = b->p[i];
+    InitArgs a{};
+    a.Lx = q.Lx;
+    a.Ly = 1;
+    a.period = its[i].period;
+    a.axis = its[i].period > 1 ? 1u : 0u;
+    a.mode = its[i].period > 1 ? uint32_t(((int64_t(q.mode_mx) % int64_t(q.Lx)) + q.Lx) % q.Lx) : 0u;
+    a.weighted = q.init_weighted ? 1u : 0u;
+    a.key0 = uint32_t(q.seed);
+    a.key1 = uint32_t(q.seed >> 32);
+    a.replica = q.replica;
+    const size_t cells = its[i].offset.size();
+    a.offset = d_all + base[i];
+    a.count = d_all + base[i] + cells;
+    a.table = d_all + base[i] + 2 * cells;
+    const int grid = int(std::min<size_t>((q.Lx + 255) / 256, size_t(b->sms) * 4));
+    e = launch_init(3, a, b->d_state + b->desc[i].state_off, grid, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(d_all);
+  if (e != cudaSuccess) return bcuda(b, e, "batch init");
+  for (auto& d : b->desc) d.t = 0;
+  BCUDA(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(ReplicaDesc) * b->n, cudaMemcpyHostToDevice, b->stream),
+        "upload desc");
+  BCUDA(b, cudaStreamSynchronize(b->stream), "batch init");
+  return ILG_OK;
+}
+
+ilg_status ilg_batch_set_state(ilg_batch* b, uint32_t i, const uint16_t* host, size_t n, uint64_t t) {
+  if (!b || !host || i >= b->n) return ILG_E_INVALID;
+  if (n != 3 * size_t(b->desc[i].L)) return bfail(b, ILG_E_INVALID, "state size must be 3 * L");
+  if (t >= (uint64_t(1) << 32)) return bfail(b, ILG_E_INVALID, "t must be below 2^32");
+  b->desc[i].t = uint32_t(t);
+  BCUDA(b, cudaMemcpyAsync(b->d_state + b->desc[i].state_off, host, sizeof(uint16_t) * n, cudaMemcpyHostToDevice, b->stream),
+        "copy state in");
+  BCUDA(b, cudaMemcpyAsync(b->d_desc + i, &b->desc[i], sizeof(ReplicaDesc), cudaMemcpyHostToDevice, b->stream), "copy desc");
+  BCUDA(b, cudaStreamSynchronize(b->stream), "copy state in");
+  return ILG_OK;
+}
+
+ilg_status ilg_batch_get_state(ilg_batch* b, uint32_t i, uint16_t* host, size_t n, uint64_t* t) {
+  if (!b || !host || i >= b->n) return ILG_E_INVALID;
+  if (n != 3 * size_t(b->desc[i].L)) return bfail(b, ILG_E_INVALID, "state size must be 3 * L");
+  BCUDA(b, cudaMemcpyAsync(host, b->d_state + b->desc[i].state_off, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost, b->stream),
+        "copy state out");
+  BCUDA(b, cudaStreamSynchronize(b->stream), "copy state out");
+  if (t) *t = b->desc[i].t;
+  return ILG_OK;
+}
+
+ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record) {
+  if (!b) return ILG_E_INVALID;
+  if (T == 0) return ILG_OK;
+  for (const auto& d : b->desc)
+    if (uint64_t(d.t) + T >= (uint64_t(1) << 32)) return bfail(b, ILG_E_INVALID, "step counter would reach 2^32");
+  const bool rec = amp_record != nullptr;
+  if (rec && b->record_cap < size_t(b->n) * T) {
+    cudaFree(b->d_record);
+    b->d_record = nullptr;
+    b->record_cap = 0;
+    BCUDA(b, cudaMalloc(&b->d_record, sizeof(double) * b->n * size_t(T)), "cudaMalloc record");
+    b->record_cap = size_t(b->n) * T;
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  if (!b->graph || b->graph_T != T || b->graph_rec != rec || b->graph_mode != record_mode) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    BatchArgs a{};
+    a.n = b->n;
+    a.T = T;
+    a.Lmax = b->Lmax;
+    a.record_mode = record_mode;
+    a.order = b->d_order;
+    a.desc = b->d_desc;
+    a.tables = b->d_tables;
+    a.state = b->d_state;
+    a.counter = b->d_counter;
+    a.failed = b->d_failed;
+    a.record = rec ? b->d_record : nullptr;
+    const int grid = int(std::min<uint32_t>(b->n, uint32_t(b->sms)));
+    cudaGraph_t g = nullptr;
+    BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_failed, 0, sizeof(uint32_t) * b->n, b->stream);
+    if (e == cudaSuccess) e = launch_batch(a, b->common, grid, b->stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bcuda(b, e != cudaSuccess ? e : e2, "capture batch launch");
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bcuda(b, e, "instantiate batch graph");
+    b->graph_T = T;
+    b->graph_rec = rec;
+    b->graph_mode = record_mode;
+  }
+  BCUDA(b, cudaGraphLaunch(b->graph, b->stream), "batch launch");
+  std::vector<uint32_t> failed(b->n);
+  BCUDA(b, cudaMemcpyAsync(failed.data(), b->d_failed, sizeof(uint32_t) * b->n, cudaMemcpyDeviceToHost, b->stream), "read flags");
+  BCUDA(b, cudaMemcpyAsync(b->desc.data(), b->d_desc, sizeof(ReplicaDesc) * b->n, cudaMemcpyDeviceToHost, b->stream), "read desc");
+  if (rec)
+    BCUDA(b, cudaMemcpyAsync(amp_record, b->d_record, sizeof(double) * b->n * size_t(T), cudaMemcpyDeviceToHost, b->stream),
+          "read record");
+  BCUDA(b, cudaStreamSynchronize(b->stream), "batch run");
+  uint32_t nf = 0, first = 0;
+  for (uint32_t i = 0; i < b->n; ++i)
+    if (failed[i]) {
+      if (!nf) first = i;
+      ++nf;
+    }
+  if (nf) {
+    char buf[200];
+    std::snprintf(buf, sizeof(buf), "%u replica(s) stopped on an occupation above 65535 (first: %u at t = %u)", nf, first,
+                  b->desc[first].t);
+    return bfail(b, ILG_E_OVERFLOW, buf);
+  }
+  return ILG_OK;
+}
+
+ilg_status ilg_batch_observables(ilg_batch* b, int32_t mode, uint64_t* mass, double* amp) {
+  if (!b) return ILG_E_INVALID;
+  BCUDA(b, launch_batch_obs(b->d_desc, b->d_state, b->n, mode, b->d_mass, b->d_amp, b->stream), "batch observables");
+  if (mass)
+    BCUDA(b, cudaMemcpyAsync(mass, b->d_mass, sizeof(uint64_t) * b->n, cudaMemcpyDeviceToHost, b->stream), "copy mass");
+  if (amp) BCUDA(b, cudaMemcpyAsync(amp, b->d_amp, sizeof(double) * b->n, cudaMemcpyDeviceToHost, b->stream), "copy amp");
+  BCUDA(b, cudaStreamSynchronize(b->stream), "batch observables");
+  return ILG_OK;
+}
+
+}  // extern "C"

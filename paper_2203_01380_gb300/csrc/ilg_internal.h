@@ -44,5 +44,7 @@ struct InitTables {
 bool build_init_tables(const ilg_params& p, int Q, InitTables* out, std::string* err);
 
 void set_context_free_error(const std::string& msg);
+std::string validate_params(const ilg_params& p);   // empty when valid
+void round_keys(uint64_t seed, uint32_t* rk);        // Philox round keys, 20 words
 
 }  // namespace ilg
