@@ -33,6 +33,17 @@ from paper_2203_01380_gb300 import inputs  # noqa: E402
 
 METRIC = "GNUPS (node-updates/s) D2Q5 ILG+flip vs HBM roofline; batched vs plain; p99"
 BYTES_PER_NU = 20  # read + write of 5 uint16 occupations
+# integer operations of the method per D2Q5 node update (two Philox4x32-10 blocks of
+# 80 int32 operations, six alias draws of 4, the redistribution split and the
+# occupation bookkeeping); the peak is one int32 lane-operation per cycle on each of
+# the 32 integer lanes (ALU + FMA-heavy pipes) of the 4 sub-partitions of 152 SMs
+OPS_PER_NU = 209
+INT_LANES_PER_SM_CYCLE = 128
+SMS = 152
+# DRAM bytes (read + write) of one 16384^2 launch of the step kernel, from the ncu
+# capture summarised in profiles/ (scaled from a 4096^2 launch by node count); None
+# when the kernel changed after the capture
+TRAFFIC_BYTES_PER_LAUNCH = 4.611e9
 
 
 def peaks():
@@ -114,6 +125,90 @@ def oracle_sample(cfg, side=512, steps=8):
     return nu, dt
 
 
+def alu_roofline(nodes, launch_ms, clocks):
+    """The step kernel is bound by integer issue: OPS_PER_NU algorithmic int32
+    operations per node update against 128 int32 lane-operations per SM per cycle
+    at the SM clock measured during the run."""
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = INT_LANES_PER_SM_CYCLE * SMS * mhz * 1e6 / 1e9          # Gop/s
+    achieved = OPS_PER_NU * nodes / (launch_ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH, "kernel": "step_vec_kernel<5, 8>", "launch_ms": launch_ms,
+            "ops_per_node_update": OPS_PER_NU, "peak_clock_mhz": mhz}
+
+
+def measure_batched(torch, B, dev):
+    """4096 D1Q3 rings, 5000 steps in one persistent launch, against one context per
+    ring on a sample of 16 rings (500 steps each) at identical results."""
+    reps = inputs.batch_replicas()
+    nodes = sum(r["Lx"] for r in reps)
+    T = 5000
+    st = torch.cuda.Stream(dev)
+    with B.Batch(reps, stream=st) as bat:
+        bat.init()
+        bat.run(20)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        bat.run(T)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+    idx = np.linspace(0, len(reps) - 1, 16).astype(int)
+    pn, t0 = 0, time.perf_counter()
+    for i in idx:
+        with B.Lattice(**reps[i], stream=st) as lat:
+            lat.init()
+            lat.step(500)
+        pn += reps[i]["Lx"] * 500
+    plain_s = time.perf_counter() - t0
+    v = nodes * T / (ms / 1e3) / 1e9
+    vp = pn / plain_s / 1e9
+    return {"workload": "batch_d1q3: 4096 rings, L log-uniform [64, 8192], n0 uniform [5, 200], "
+                        "omega_eff uniform [0.2, 1.95], 5000 steps, one persistent graph-captured launch",
+            "value": v, "unit": "GNUPS", "ms": ms, "node_updates": nodes * T,
+            "plain_per_ring_launch": {"value": vp, "unit": "GNUPS",
+                                      "sample": "16 rings (evenly spaced in the list), init + 500 steps each, one context each, host wall clock"},
+            "speedup_vs_plain": v / vp}
+
+
+def measure_serving(B, n_requests=200):
+    """Poisson arrivals (200/s) of D2Q5 requests, submitted in real time."""
+    reqs = inputs.serve_requests(n_requests)
+    tot = sum(r["Lx"] * r["Ly"] * r["steps"] for r in reqs)
+    with B.Server(5, 48 << 30, max_slots=512, quantum=32) as srv:
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            dt = r["arrive"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            srv.submit(i, **{k: v for k, v in r.items() if k != "arrive"})
+        srv.wait_idle(1800)
+        wall = time.perf_counter() - t0
+        res = srv.poll(4096)
+        st = srv.stats()
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+    queue = np.array([r["t_admit"] - r["t_submit"] for r in res])
+    # the same requests one after another, one context each (every 4th request)
+    pn, t0 = 0, time.perf_counter()
+    for r in reqs[::4]:
+        with B.Lattice(**{k: v for k, v in r.items() if k not in ("arrive", "steps")}) as one:
+            one.init()
+            one.step(r["steps"])
+            one.observables([(1, 0)])
+        pn += r["Lx"] * r["Ly"] * r["steps"]
+    plain_s = time.perf_counter() - t0
+    return {"workload": f"serve_d2q5: {n_requests} requests, Poisson arrivals 200/s, side log-uniform [64, 2048], "
+                        "steps log-uniform [100, 10000], n0 uniform [5, 100], omega_eff 1.5",
+            "aggregate": {"value": tot / wall / 1e9, "unit": "GNUPS"}, "offered_node_updates": tot,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "queueing_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+            "completed": len(res), "wall_s": wall, "peak_resident": st["peak_resident"],
+            "plain_one_context_per_request": {"value": pn / plain_s / 1e9, "unit": "GNUPS",
+                                              "sample": "every 4th request, run alone one after another"}}
+
+
 def run_reference(args, cfg, world, rank):
     if rank != 0:
         return
@@ -147,6 +242,7 @@ def main():
     ap.add_argument("--tsteps", type=int, default=inputs.LARGE_D2Q5["steps"], help="lattice steps per bench step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="skip the batched and serving measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     cfg = {k: v for k, v in inputs.LARGE_D2Q5.items() if k != "steps"}
@@ -236,6 +332,11 @@ def main():
                "h2d_bytes_per_step": int(lat.size * 2 + 8 * len(modes)),
                "d2h_bytes_per_step": int(lat.size * 2 + 8 + 32 * len(modes))}
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_modes:
+        extra["batched"] = measure_batched(torch, B, dev)
+        extra["serving"] = measure_serving(B)
+
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         side, csteps = 512, 8
@@ -262,12 +363,13 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
-                         "frac": achieved_gbs / peak, "traffic": None,
-                         "kernel": "step_generic_kernel<5>", "launch_ms": launch_ms,
-                         "algorithmic_bytes_per_launch": nodes * BYTES_PER_NU},
+            "roofline": alu_roofline(nodes, launch_ms, clk.summary()),
+            "hbm": {"achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
+                    "algorithmic_bytes_per_launch": nodes * BYTES_PER_NU, "peak_source": "MEASURED_PEAKS.json hbm_gbs"
+                    if pk else "fallback 6800"},
             "observables_ms_per_step": obs_ms / args.steps,
             "cpu_baseline": cpu,
+            **extra,
             "check": {"mass": obs["mass"], "t": obs["t"]},
         }
         print(json.dumps(line), flush=True)

@@ -154,6 +154,50 @@ ilg_status ilg_batch_get_state(ilg_batch* b, uint32_t i, uint16_t* host, size_t 
 ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record);
 ilg_status ilg_batch_observables(ilg_batch* b, int32_t mode, uint64_t* mass, double* amp);
 
+/* ---------------------------------------------------------------------------
+ * Serving loop for D2Q5 lattice requests (continuous batching).  A worker thread
+ * admits requests in arrival order while a free slot and room in a device arena
+ * of hbm_bytes (allocated once, here) allow, keeps admitted lattices resident, and
+ * advances all of them together: one launch per time step, `quantum` steps per
+ * round (fewer when a request needs fewer), so newcomers join the next round.  A
+ * finished request's observables go to the result queue and, if final_state was
+ * given, its state (5*Lx*Ly uint16) is copied there; its memory returns to the
+ * arena.  Results equal those of the request run alone (ilg_create ...), bit for
+ * bit.  All requests share the server's seed.  Host waits only (no device spin).
+ *   ilg_server_create    seed, arena bytes, slots, quantum, stream (NULL: private)
+ *   ilg_server_submit    thread-safe, returns at once; final_state must stay valid
+ *                        until the request's result has been polled
+ *   ilg_server_poll      up to cap finished results (and their count in *n)
+ *   ilg_server_wait_idle until every submitted request has finished (ILG_E_TIMEOUT)
+ *   ilg_server_stats     worker busy time (s), node updates done, peak residents
+ * Result fields: id, status (ILG_OK, ILG_E_OVERFLOW: stopped before the step that
+ * would exceed 65535, ILG_E_INVALID: bad initial means), t (final step counter),
+ * mass, amp = A^LG and Sk = S(k) of mode (1, 0), times in seconds on the server's
+ * clock: submitted, admitted, done.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+  uint64_t id;
+  int32_t status;
+  uint32_t reserved;
+  uint64_t t;
+  uint64_t mass;
+  double amp;
+  double Sk;
+  double t_submit;
+  double t_admit;
+  double t_done;
+} ilg_result;
+typedef struct ilg_server ilg_server;
+ilg_status ilg_server_create(uint64_t seed, uint64_t hbm_bytes, uint32_t max_slots, uint32_t quantum, void* stream,
+                             ilg_server** out);
+ilg_status ilg_server_submit(ilg_server* s, uint64_t id, const ilg_params* params, uint32_t steps,
+                             uint16_t* final_state);
+ilg_status ilg_server_poll(ilg_server* s, ilg_result* out, uint32_t cap, uint32_t* n);
+ilg_status ilg_server_wait_idle(ilg_server* s, double timeout_s);
+ilg_status ilg_server_stats(ilg_server* s, double* busy_s, double* node_updates, uint32_t* peak_resident);
+ilg_status ilg_server_destroy(ilg_server* s);
+const char* ilg_server_last_error(const ilg_server* s);
+
 /* Observables of a state in caller-owned device memory, allocating nothing (the
  * paper has no counterpart; this serves callers that cannot allocate device memory
  * when they need the numbers: code running while a stream is captured into a CUDA

@@ -73,6 +73,22 @@ _lib.ilg_batch_set_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t,
 _lib.ilg_batch_get_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
 _lib.ilg_batch_run.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp]
 _lib.ilg_batch_observables.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("t", ctypes.c_uint64), ("mass", ctypes.c_uint64), ("amp", ctypes.c_double), ("Sk", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+_lib.ilg_server_create.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _vp,
+                                   ctypes.POINTER(_vp)]
+_lib.ilg_server_submit.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(Params), ctypes.c_uint32, _vp]
+_lib.ilg_server_poll.argtypes = [_vp, ctypes.POINTER(Result), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+_lib.ilg_server_wait_idle.argtypes = [_vp, ctypes.c_double]
+_lib.ilg_server_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_uint32)]
+_lib.ilg_server_destroy.argtypes = [_vp]
+_lib.ilg_server_last_error.argtypes = [_vp]
+_lib.ilg_server_last_error.restype = ctypes.c_char_p
 _lib.ilg_philox.argtypes = [_u32p, ctypes.c_uint64, _u32p, ctypes.c_size_t, _vp]
 _lib.ilg_binomial_table.argtypes = [ctypes.c_uint64, _u32p]
 _lib.ilg_alias_table.argtypes = [ctypes.c_uint64, _u32p, _u32p]
@@ -80,7 +96,9 @@ _lib.ilg_poisson_table.argtypes = [ctypes.c_double, _u32p, ctypes.c_uint32, ctyp
 for _f in ("ilg_create", "ilg_destroy", "ilg_init", "ilg_set_state", "ilg_set_state_device", "ilg_get_state",
            "ilg_get_state_device", "ilg_step", "ilg_observables", "ilg_philox", "ilg_binomial_table",
            "ilg_alias_table", "ilg_poisson_table", "ilg_observables_noalloc", "ilg_batch_create", "ilg_batch_destroy",
-           "ilg_batch_init", "ilg_batch_set_state", "ilg_batch_get_state", "ilg_batch_run", "ilg_batch_observables"):
+           "ilg_batch_init", "ilg_batch_set_state", "ilg_batch_get_state", "ilg_batch_run", "ilg_batch_observables",
+           "ilg_server_create", "ilg_server_submit", "ilg_server_poll", "ilg_server_wait_idle", "ilg_server_stats",
+           "ilg_server_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -248,6 +266,68 @@ class Batch:
         amp = np.zeros(self.n)
         self._check(_lib.ilg_batch_observables(self._h, int(mode), mass.ctypes.data, amp.ctypes.data))
         return mass, amp
+
+
+class Server:
+    """Serving loop for D2Q5 requests (ilg_server_*)."""
+
+    def __init__(self, seed, hbm_bytes, max_slots=256, quantum=32, stream=None):
+        h = _vp()
+        st = _lib.ilg_server_create(int(seed), int(hbm_bytes), int(max_slots), int(quantum),
+                                    _vp(stream_handle(stream)), ctypes.byref(h))
+        if st != ILG_OK:
+            raise IlgError(st, _lib.ilg_server_last_error(None).decode(errors="replace"))
+        self._h = h
+        self._states = {}   # id -> host buffer receiving the final state
+
+    def _check(self, st):
+        if st != ILG_OK:
+            raise IlgError(st, _lib.ilg_server_last_error(self._h).decode(errors="replace"))
+
+    def submit(self, rid, steps, want_state=False, **params):
+        p = make_params(**params)
+        buf = None
+        if want_state:
+            buf = np.zeros((5, p.Ly, p.Lx), dtype=np.uint16)
+            self._states[rid] = buf
+        self._check(_lib.ilg_server_submit(self._h, int(rid), ctypes.byref(p), int(steps),
+                                           buf.ctypes.data if buf is not None else None))
+
+    def poll(self, cap=1024):
+        out = (Result * cap)()
+        n = ctypes.c_uint32()
+        self._check(_lib.ilg_server_poll(self._h, out, cap, ctypes.byref(n)))
+        res = []
+        for r in out[:n.value]:
+            d = {k: getattr(r, k) for k, _ in Result._fields_ if k != "reserved"}
+            d["state"] = self._states.pop(r.id, None)
+            res.append(d)
+        return res
+
+    def wait_idle(self, timeout_s=600.0):
+        self._check(_lib.ilg_server_wait_idle(self._h, float(timeout_s)))
+
+    def stats(self):
+        b, nu, pk = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint32()
+        self._check(_lib.ilg_server_stats(self._h, ctypes.byref(b), ctypes.byref(nu), ctypes.byref(pk)))
+        return dict(busy_s=b.value, node_updates=nu.value, peak_resident=pk.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ilg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def observables_noalloc(lattice: int, Lx: int, Ly: int, state_dev_ptr: int, modes=(), stream=None):

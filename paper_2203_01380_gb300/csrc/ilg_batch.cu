@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, Ste
 
 }  // namespace
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 1024;
 
 size_t batch_smem_bytes(uint32_t Lmax) {
   return sizeof(uint32_t) * kDevBlockWords + sizeof(uint16_t) * 2 * 3 * size_t(Lmax);

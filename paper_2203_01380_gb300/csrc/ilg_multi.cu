@@ -1,0 +1,134 @@
+// Multi-lattice step: one launch advances every resident lattice of a server by one
+// time step.  Work items are runs of up to kRowsPerItem rows of one lattice; blocks
+// pull items from a queue and reload the alias tables only when the lattice
+// changes.  Threads walk a row's nodes (any extent): load the Q occupations, flip,
+// collide, and scatter n'_i to x + v_i (periodic).  Each lattice keeps its own step
+// counter, replica word and two buffers, so its result is the one it would have
+// had alone.
+#include <cuda_runtime.h>
+
+#include "ilg_device.cuh"
+#include "ilg_multi.h"
+
+namespace ilg {
+
+namespace {
+
+// Rows [row0, row1) of one lattice: the block's threads walk all their nodes
+// together (so short rows keep every thread busy), load the Q occupations, flip,
+// collide and scatter n'_i to x + v_i (periodic).
+template <int Q>
+__device__ __forceinline__ void step_rows(const StepArgs& a, const uint32_t* s, const uint16_t* __restrict__ in,
+                                          uint16_t* __restrict__ out, uint32_t row0, uint32_t row1, uint32_t t,
+                                          bool& bad) {
+  const uint32_t Lx = a.Lx, Ly = a.Ly;
+  const size_t plane = size_t(Lx) * Ly;
+  const uint32_t count = (row1 - row0) * Lx;
+  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const uint32_t dy = i / Lx;
+    const uint32_t x = i - dy * Lx;
+    const uint32_t y = row0 + dy;
+    const size_t row = size_t(y) * Lx;
+    const size_t at = row + x;
+    uint32_t n[Q], m[Q], post[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) n[k] = in[k * plane + at];
+    m[0] = n[0];
+    m[1] = a.flip ? n[2] : n[1];
+    m[2] = a.flip ? n[1] : n[2];
+    if constexpr (Q == 5) {
+      m[3] = a.flip ? n[4] : n[3];
+      m[4] = a.flip ? n[3] : n[4];
+    }
+    if (!collide_try_fast<Q>(a, s, uint32_t(at), t, m, post)) {
+      collide<Q>(a, s, uint32_t(at), t, m, post);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) bad |= post[k] > 65535u;
+    }
+    const uint32_t xp = x + 1 == Lx ? 0 : x + 1;
+    const uint32_t xm = x == 0 ? Lx - 1 : x - 1;
+    out[at] = uint16_t(post[0]);
+    out[plane + row + xp] = uint16_t(post[1]);
+    out[2 * plane + row + xm] = uint16_t(post[2]);
+    if constexpr (Q == 5) {
+      const uint32_t yp = y + 1 == Ly ? 0 : y + 1;
+      const uint32_t ym = y == 0 ? Ly - 1 : y - 1;
+      out[3 * plane + size_t(yp) * Lx + x] = uint16_t(post[3]);
+      out[4 * plane + size_t(ym) * Lx + x] = uint16_t(post[4]);
+    }
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kMultiThreads, 4) multi_step_kernel(MultiArgs ma, StepArgs common,
+                                                                      uint32_t sub) {
+  extern __shared__ uint4 smem4[];
+  uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
+  __shared__ uint32_t s_item;
+  int loaded = -1;
+  uint32_t next = 0, end = 0;  // the block's current run of consecutive items
+  for (;;) {
+    if (threadIdx.x == 0) {
+      // runs of kItemsPerGrab consecutive items (mostly one lattice: few table reloads);
+      // skip lattices that overflowed in an earlier sub-step or are done for this round
+      uint32_t it = ma.n_items;
+      for (;;) {
+        if (next >= end) {
+          next = atomicAdd(ma.counter + sub, kItemsPerGrab);
+          end = min(next + kItemsPerGrab, ma.n_items);
+        }
+        if (next >= ma.n_items) break;
+        const uint32_t lat = ma.items[next].lattice;
+        if (ma.fail[lat] < sub || sub >= ma.lat[lat].steps) {
+          ++next;
+          continue;
+        }
+        it = next++;
+        break;
+      }
+      s_item = it;
+    }
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= ma.n_items) break;
+    const WorkItem w = ma.items[item];
+    const LatDesc d = ma.lat[w.lattice];
+    if (int(w.lattice) != loaded) {
+      const uint4* g4 = reinterpret_cast<const uint4*>(d.tables);
+      for (uint32_t i = threadIdx.x; i < kDevBlockWords / 4; i += blockDim.x) smem4[i] = g4[i];
+      loaded = int(w.lattice);
+    }
+    __syncthreads();
+    StepArgs a = common;
+    a.Lx = d.Lx;
+    a.Ly = d.Ly;
+    a.flip = d.flip;
+    a.omega_mode = d.omega_mode;
+    a.rest_mode = d.rest_mode;
+    a.replica = d.replica;
+    const uint32_t t = d.t0 + sub;
+    const bool odd = ((sub + d.phase) & 1u) != 0;
+    const uint16_t* in = odd ? d.buf1 : d.buf0;
+    uint16_t* out = odd ? d.buf0 : d.buf1;
+    bool bad = false;
+    step_rows<Q>(a, s, in, out, w.row0, w.row1, t, bad);
+    if (bad) atomicMin(ma.fail + w.lattice, sub);
+    __syncthreads();  // the tables and s_item stay in use until every thread is done
+  }
+}
+
+}  // namespace
+
+size_t multi_smem_bytes() { return sizeof(uint32_t) * kDevBlockWords; }
+
+cudaError_t prepare_multi_kernel() {
+  return cudaFuncSetAttribute(multi_step_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(multi_smem_bytes()));
+}
+
+cudaError_t launch_multi_step(const MultiArgs& ma, const StepArgs& common, uint32_t sub, int grid, cudaStream_t s) {
+  multi_step_kernel<5><<<grid, kMultiThreads, multi_smem_bytes(), s>>>(ma, common, sub);
+  return cudaGetLastError();
+}
+
+}  // namespace ilg
