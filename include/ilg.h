@@ -112,6 +112,13 @@ ilg_status ilg_get_state_device(ilg_ctx* ctx, uint16_t* dev, size_t n, uint64_t*
  * the last completed step before the failing one. */
 ilg_status ilg_step(ilg_ctx* ctx, uint32_t T);
 
+/* Temporal blocking (D2Q5): with depth >= 2, ilg_step runs blocks of `depth` steps
+ * per launch (48 x 48 tiles with a halo of depth nodes, recomputed, held in shared
+ * memory) and single steps for the remainder; results are bit-identical to single
+ * steps.  depth 0 or 1 switches it off (the default); at most 8.  On
+ * ILG_E_OVERFLOW the state is the input of the failing launch. */
+ilg_status ilg_set_temporal_blocking(ilg_ctx* ctx, uint32_t depth);
+
 /* Observables of the current state (Sec. V).  modes: nmodes pairs (mx, my), each an
  * axis mode (one of the two zero, not both).  For a mode along x with
  * D(x) = Lx*C(x) - M, C(x) = sum_y N(x,y), r = (mx*x) mod Lx:

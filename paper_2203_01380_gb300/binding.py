@@ -59,6 +59,7 @@ _lib.ilg_set_state_device.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_uint64
 _lib.ilg_get_state.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
 _lib.ilg_get_state_device.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
 _lib.ilg_step.argtypes = [_vp, ctypes.c_uint32]
+_lib.ilg_set_temporal_blocking.argtypes = [_vp, ctypes.c_uint32]
 _lib.ilg_observables.argtypes = [_vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(ctypes.c_uint64), _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.ilg_observables_noalloc.argtypes = [ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp,
@@ -93,7 +94,7 @@ _lib.ilg_philox.argtypes = [_u32p, ctypes.c_uint64, _u32p, ctypes.c_size_t, _vp]
 _lib.ilg_binomial_table.argtypes = [ctypes.c_uint64, _u32p]
 _lib.ilg_alias_table.argtypes = [ctypes.c_uint64, _u32p, _u32p]
 _lib.ilg_poisson_table.argtypes = [ctypes.c_double, _u32p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
-for _f in ("ilg_create", "ilg_destroy", "ilg_init", "ilg_set_state", "ilg_set_state_device", "ilg_get_state",
+for _f in ("ilg_set_temporal_blocking", "ilg_create", "ilg_destroy", "ilg_init", "ilg_set_state", "ilg_set_state_device", "ilg_get_state",
            "ilg_get_state_device", "ilg_step", "ilg_observables", "ilg_philox", "ilg_binomial_table",
            "ilg_alias_table", "ilg_poisson_table", "ilg_observables_noalloc", "ilg_batch_create", "ilg_batch_destroy",
            "ilg_batch_init", "ilg_batch_set_state", "ilg_batch_get_state", "ilg_batch_run", "ilg_batch_observables",
@@ -192,6 +193,9 @@ class Lattice:
 
     def step(self, T: int):
         _check(_lib.ilg_step(self._h, int(T)), self._h)
+
+    def set_temporal_blocking(self, depth: int):
+        _check(_lib.ilg_set_temporal_blocking(self._h, int(depth)), self._h)
 
     def observables(self, modes=(), col_sums=False, row_sums=False):
         modes = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, 2))

@@ -1,6 +1,7 @@
 // C ABI of libilg.so: contexts, validation, scheduling of the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -34,6 +35,7 @@ struct ilg_ctx {
   int32_t* d_modes = nullptr;
   double* d_res = nullptr;
   uint32_t mode_cap = 0;
+  uint32_t tb_depth = 0;                   // temporal blocking: steps per launch (0: off)
   unsigned long long* h_word = nullptr;    // pinned 8-byte readback
   std::string err;
 };
@@ -315,6 +317,15 @@ ilg_status ilg_get_state_device(ilg_ctx* c, uint16_t* dev, size_t n, uint64_t* t
   return get_state_impl(c, dev, n, t, cudaMemcpyDeviceToDevice);
 }
 
+ilg_status ilg_set_temporal_blocking(ilg_ctx* c, uint32_t depth) {
+  if (!c) return ILG_E_INVALID;
+  if (depth > kMaxTbDepth) return fail(c, ILG_E_INVALID, "temporal blocking depth above 8");
+  if (depth >= 2 && c->Q != 5) return fail(c, ILG_E_INVALID, "temporal blocking is for D2Q5 lattices");
+  if (depth >= 2) ILG_CUDA(c, prepare_step_tb_kernel(kTbTile, depth), "cudaFuncSetAttribute");
+  c->tb_depth = depth >= 2 ? depth : 0;
+  return ILG_OK;
+}
+
 ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   if (!c) return ILG_E_INVALID;
   if (!c->has_state) return fail(c, ILG_E_STATE, "no state: call ilg_init or ilg_set_state first");
@@ -325,13 +336,32 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   const int grid = vec ? vec_grid(c) : step_grid(c);
   const int cur0 = c->cur;
   const uint64_t t0 = c->t;
+  // launches: blocks of tb_depth steps (temporal blocking), then single steps;
+  // launch_t[k] is the step a launch starts from, its input is buffer cur0 ^ (k & 1)
+  std::vector<uint64_t> launch_t;
   int cur = cur0;
-  for (uint32_t s = 0; s < T; ++s) {
-    cudaError_t e = vec ? launch_step_vec(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t0 + s), c->d_fail,
-                                          grid, c->stream)
-                        : launch_step(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t0 + s), c->d_fail, grid,
+  uint64_t t = t0;
+  const uint32_t tb = c->tb_depth;
+  if (tb >= 2) {
+    const size_t tiles = size_t((c->p.Lx + kTbTile - 1) / kTbTile) * ((c->p.Ly + kTbTile - 1) / kTbTile);
+    const int tgrid = int(std::min<size_t>(tiles, size_t(c->sms) * 2));
+    for (uint32_t k = 0; k + tb <= T; k += tb) {
+      cudaError_t e = launch_step_tb(a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), tb, kTbTile, c->d_fail, tgrid,
+                                     c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "temporal blocking kernel");
+      launch_t.push_back(t);
+      t += tb;
+      cur ^= 1;
+    }
+  }
+  while (t < t0 + T) {
+    cudaError_t e = vec ? launch_step_vec(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid,
+                                          c->stream)
+                        : launch_step(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid,
                                       c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+    launch_t.push_back(t);
+    t += 1;
     cur ^= 1;
   }
   ILG_CUDA(c, cudaMemcpyAsync(c->h_word, c->d_fail, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
@@ -339,13 +369,15 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   ILG_CUDA(c, cudaStreamSynchronize(c->stream), "step");
   const unsigned long long f = *c->h_word;
   if (f != ~0ull) {
-    // step f failed: its input buffer still holds the state at step f
-    c->cur = cur0 ^ int((f - t0) & 1u);
+    // the launch that started at step f failed: its input buffer still holds the state at f
+    size_t k = 0;
+    while (k < launch_t.size() && launch_t[k] != f) ++k;
+    c->cur = cur0 ^ int(k & 1u);
     c->t = f;
     ILG_CUDA(c, cudaMemsetAsync(c->d_fail, 0xFF, sizeof(unsigned long long), c->stream), "reset flag");
     ILG_CUDA(c, cudaStreamSynchronize(c->stream), "reset flag");
     char buf[160];
-    std::snprintf(buf, sizeof(buf), "occupation above 65535 in step %llu; state kept at t = %llu", f, f);
+    std::snprintf(buf, sizeof(buf), "occupation above 65535 in the launch from step %llu; state kept at t = %llu", f, f);
     return fail(c, ILG_E_OVERFLOW, buf);
   }
   c->cur = cur;

@@ -13,6 +13,8 @@ constexpr uint32_t kNmax = 64;                              // trials per binomi
 constexpr uint32_t kTableWords = kNmax * (kNmax + 1) / 2;   // 2080 entries
 constexpr uint32_t kPoissonCap = 4096;                       // entries per Poisson table
 constexpr double kMaxMean = 700.0;                           // largest initial mean
+constexpr uint32_t kMaxTbDepth = 8;                          // temporal blocking: steps per launch
+constexpr uint32_t kTbTile = 48;                             // temporal blocking: tile side
 
 // Philox purpose tags (top 8 bits of the fourth counter word).
 constexpr uint32_t kTagStep = 1;

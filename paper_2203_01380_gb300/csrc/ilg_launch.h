@@ -29,6 +29,10 @@ cudaError_t prepare_step_vec_kernels();
 uint32_t step_vec_width();  // nodes per thread of the row-tiled step (rows must be a multiple)
 cudaError_t launch_step_vec(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                             unsigned long long* fail, int grid, cudaStream_t s);
+size_t step_tb_smem_bytes(uint32_t B, uint32_t Tb);
+cudaError_t prepare_step_tb_kernel(uint32_t B, uint32_t Tb);
+cudaError_t launch_step_tb(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t0, uint32_t Tb,
+                           uint32_t B, unsigned long long* fail, int grid, cudaStream_t s);
 cudaError_t launch_init(int Q, const InitArgs& a, uint16_t* out, int grid, cudaStream_t s);
 cudaError_t launch_sums(int Q, const uint16_t* in, uint32_t Lx, uint32_t Ly, unsigned long long* col,
                         unsigned long long* row, int want_rows, cudaStream_t s);

@@ -1,7 +1,7 @@
 // Multi-lattice step: one launch advances every resident lattice of a server by one
-// time step.  Work items are runs of up to kRowsPerItem rows of one lattice; blocks
-// pull items from a queue and reload the alias tables only when the lattice
-// changes.  Threads walk a row's nodes (any extent): load the Q occupations, flip,
+// time step.  Work items are runs of about kItemNodes consecutive nodes of one
+// lattice; blocks pull items one at a time from a queue and reload the alias tables
+// only when the lattice changes.  Threads walk the nodes: load the Q occupations, flip,
 // collide, and scatter n'_i to x + v_i (periodic).  Each lattice keeps its own step
 // counter, replica word and two buffers, so its result is the one it would have
 // had alone.
@@ -14,20 +14,18 @@ namespace ilg {
 
 namespace {
 
-// Rows [row0, row1) of one lattice: the block's threads walk all their nodes
-// together (so short rows keep every thread busy), load the Q occupations, flip,
-// collide and scatter n'_i to x + v_i (periodic).
+// Nodes [node0, node1) of one lattice (row-major): the block's threads walk them
+// together, load the Q occupations, flip, collide and scatter n'_i to x + v_i
+// (periodic).
 template <int Q>
-__device__ __forceinline__ void step_rows(const StepArgs& a, const uint32_t* s, const uint16_t* __restrict__ in,
-                                          uint16_t* __restrict__ out, uint32_t row0, uint32_t row1, uint32_t t,
-                                          bool& bad) {
+__device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s, const uint16_t* __restrict__ in,
+                                           uint16_t* __restrict__ out, uint32_t node0, uint32_t node1, uint32_t t,
+                                           bool& bad) {
   const uint32_t Lx = a.Lx, Ly = a.Ly;
   const size_t plane = size_t(Lx) * Ly;
-  const uint32_t count = (row1 - row0) * Lx;
-  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
-    const uint32_t dy = i / Lx;
-    const uint32_t x = i - dy * Lx;
-    const uint32_t y = row0 + dy;
+  for (uint32_t nd = node0 + threadIdx.x; nd < node1; nd += blockDim.x) {
+    const uint32_t y = nd / Lx;
+    const uint32_t x = nd - y * Lx;
     const size_t row = size_t(y) * Lx;
     const size_t at = row + x;
     uint32_t n[Q], m[Q], post[Q];
@@ -66,26 +64,13 @@ __global__ void __launch_bounds__(kMultiThreads, 4) multi_step_kernel(MultiArgs 
   uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
   __shared__ uint32_t s_item;
   int loaded = -1;
-  uint32_t next = 0, end = 0;  // the block's current run of consecutive items
   for (;;) {
     if (threadIdx.x == 0) {
-      // runs of kItemsPerGrab consecutive items (mostly one lattice: few table reloads);
       // skip lattices that overflowed in an earlier sub-step or are done for this round
-      uint32_t it = ma.n_items;
-      for (;;) {
-        if (next >= end) {
-          next = atomicAdd(ma.counter + sub, kItemsPerGrab);
-          end = min(next + kItemsPerGrab, ma.n_items);
-        }
-        if (next >= ma.n_items) break;
-        const uint32_t lat = ma.items[next].lattice;
-        if (ma.fail[lat] < sub || sub >= ma.lat[lat].steps) {
-          ++next;
-          continue;
-        }
-        it = next++;
-        break;
-      }
+      uint32_t it = atomicAdd(ma.counter + sub, 1u);
+      while (it < ma.n_items &&
+             (ma.fail[ma.items[it].lattice] < sub || sub >= ma.lat[ma.items[it].lattice].steps))
+        it = atomicAdd(ma.counter + sub, 1u);
       s_item = it;
     }
     __syncthreads();
@@ -111,7 +96,7 @@ __global__ void __launch_bounds__(kMultiThreads, 4) multi_step_kernel(MultiArgs 
     const uint16_t* in = odd ? d.buf1 : d.buf0;
     uint16_t* out = odd ? d.buf0 : d.buf1;
     bool bad = false;
-    step_rows<Q>(a, s, in, out, w.row0, w.row1, t, bad);
+    step_nodes<Q>(a, s, in, out, w.node0, w.node1, t, bad);
     if (bad) atomicMin(ma.fail + w.lattice, sub);
     __syncthreads();  // the tables and s_item stay in use until every thread is done
   }

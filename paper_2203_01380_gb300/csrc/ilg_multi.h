@@ -11,8 +11,7 @@
 namespace ilg {
 
 constexpr int kMultiThreads = 256;
-constexpr uint32_t kItemNodes = 4096;  // nodes per work item (whole rows, at least one)
-constexpr uint32_t kItemsPerGrab = 8;  // consecutive items a block takes from the queue at once
+constexpr uint32_t kItemNodes = 1024;  // nodes per work item (a run of consecutive nodes of one lattice)
 
 struct LatDesc {
   uint32_t Lx, Ly;
@@ -28,7 +27,7 @@ struct LatDesc {
 };
 
 struct WorkItem {
-  uint32_t lattice, row0, row1;
+  uint32_t lattice, node0, node1;  // nodes [node0, node1) of the lattice, row-major
 };
 
 struct MultiArgs {

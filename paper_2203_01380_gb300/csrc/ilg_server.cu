@@ -338,8 +338,8 @@ void worker_main(ilg_server* s) {
       const uint32_t li = uint32_t(lat.size());
       lat.push_back(d);
       which.push_back(k);
-      const uint32_t rows = std::max<uint32_t>(1u, kItemNodes / d.Lx);
-      for (uint32_t y = 0; y < d.Ly; y += rows) items.push_back(WorkItem{li, y, std::min(d.Ly, y + rows)});
+      const uint32_t nodes = d.Lx * d.Ly;
+      for (uint32_t n0 = 0; n0 < nodes; n0 += kItemNodes) items.push_back(WorkItem{li, n0, std::min(nodes, n0 + kItemNodes)});
     }
     if (!lat.empty() && q > 0) {
       if (items.size() > s->items_cap) {
