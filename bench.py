@@ -106,6 +106,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_workload(cfg: dict, rank: int) -> dict:
+    """Weak scaling: every rank advances its own lattice of the workload, told apart
+    by the replica word of its random numbers."""
+    c = dict(cfg)
+    c["replica"] = rank
+    return c
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (the job's time); no reduction with one rank."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -256,7 +275,8 @@ def main():
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     cfg = {k: v for k, v in inputs.LARGE_D2Q5.items() if k != "steps"}
-    cfg.update(Lx=args.side, Ly=args.side, replica=rank)
+    cfg.update(Lx=args.side, Ly=args.side)
+    cfg = rank_workload(cfg, rank)
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)
         return
@@ -301,13 +321,9 @@ def main():
             e2.record(stream)
         end.record(stream)
         barrier()
-    total_ms = start.elapsed_time(end)
+    total_ms = max_over_ranks(start.elapsed_time(end), world, dev)
     step_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
     obs_ms = sum(b.elapsed_time(c) for _, b, c in ev)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
     nu = float(nodes) * T * args.steps * world
     value = nu / (total_ms / 1e3) / 1e9
     launch_ms = step_ms / (T * args.steps)
@@ -333,11 +349,7 @@ def main():
             lat.get_state(res.reshape(lat.shape))
         e_end.record(stream)
         barrier()
-        e_ms = e_start.elapsed_time(e_end)
-        if world > 1:
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
+        e_ms = max_over_ranks(e_start.elapsed_time(e_end), world, dev)
         e2e = {"value": nu / (e_ms / 1e3) / 1e9, "unit": "GNUPS",
                "h2d_bytes_per_step": int(lat.size * 2 + 8 * len(modes)),
                "d2h_bytes_per_step": int(lat.size * 2 + 8 + 32 * len(modes))}
