@@ -95,13 +95,12 @@ struct FastCollide {
   }
 };
 
-// flip and collide one node on the fast path (no result there exceeds 65535);
-// returns false when the node needs the general collision (post is then 0)
+// collide one node (occupations m, already flipped) on the fast path (no result
+// there exceeds 65535); returns false when the node needs the general collision
+// (post is then 0)
 template <int Q, class Coll>
 __device__ __forceinline__ bool node_update(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
-                                            const uint32_t (&n)[Q], uint32_t (&post)[Q]) {
-  uint32_t m[Q];
-  flip<Q>(a, n, m);
+                                            const uint32_t (&m)[Q], uint32_t (&post)[Q]) {
   const bool ok = Coll::template run<Q>(a, s, node, t, m, post);
 #pragma unroll
   for (int i = 0; i < Q; ++i) post[i] = ok ? post[i] : 0u;
@@ -149,6 +148,20 @@ __global__ void __launch_bounds__(THREADS, MINB)
         Vec<NPT> N[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) N[i] = vload<NPT>(in + i * plane + rowoff + x0);
+        if (a.flip) {
+          // the flip F_i(n) = n_{-i} swaps whole opposite planes of the vector
+#pragma unroll
+          for (int j = 0; j < NPT / 2; ++j) {
+            const uint32_t p = N[1].w[j];
+            N[1].w[j] = N[2].w[j];
+            N[2].w[j] = p;
+            if constexpr (Q == 5) {
+              const uint32_t q = N[3].w[j];
+              N[3].w[j] = N[4].w[j];
+              N[4].w[j] = q;
+            }
+          }
+        }
         uint32_t slow = 0;  // nodes that need the general collision
         if constexpr (UNROLL) {
 #pragma unroll
