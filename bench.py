@@ -191,11 +191,10 @@ def measure_batched(torch, B, dev):
             "speedup_vs_plain": v / vp}
 
 
-def measure_serving(B, n_requests=200):
-    """Poisson arrivals (200/s) of D2Q5 requests, submitted in real time."""
-    reqs = inputs.serve_requests(n_requests)
-    tot = sum(r["Lx"] * r["Ly"] * r["steps"] for r in reqs)
-    with B.Server(5, 48 << 30, max_slots=512, quantum=32) as srv:
+def serve_stream(B, reqs, slots, smallest_first):
+    """Submit requests at their arrival times; returns results, wall time, stats."""
+    with B.Server(5, 48 << 30, max_slots=slots, quantum=32) as srv:
+        srv.set_policy(smallest_first)
         t0 = time.perf_counter()
         for i, r in enumerate(reqs):
             dt = r["arrive"] - (time.perf_counter() - t0)
@@ -206,8 +205,26 @@ def measure_serving(B, n_requests=200):
         wall = time.perf_counter() - t0
         res = srv.poll(4096)
         st = srv.stats()
+    return res, wall, st
+
+
+def latency_summary(res):
     lat = np.array([r["t_done"] - r["t_submit"] for r in res])
     queue = np.array([r["t_admit"] - r["t_submit"] for r in res])
+    return ({"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))})
+
+
+def measure_serving(B, n_requests=200):
+    """Poisson arrivals (200/s) of D2Q5 requests, submitted in real time: every
+    request admitted at once (arrival order), and least-work-first admission into 32
+    slots."""
+    reqs = inputs.serve_requests(n_requests)
+    tot = sum(r["Lx"] * r["Ly"] * r["steps"] for r in reqs)
+    res, wall, st = serve_stream(B, reqs, 512, False)
+    lat_all, queue_all = latency_summary(res)
+    res2, wall2, st2 = serve_stream(B, reqs, 32, True)
+    lat_sm, queue_sm = latency_summary(res2)
     # the same subset (every 4th request) served together and run one after another,
     # one context each, at identical results
     sub = reqs[::4]
@@ -228,10 +245,11 @@ def measure_serving(B, n_requests=200):
     return {"workload": f"serve_d2q5: {n_requests} requests, Poisson arrivals 200/s, side log-uniform [64, 2048], "
                         "steps log-uniform [100, 10000], n0 uniform [5, 100], omega_eff 1.5",
             "aggregate": {"value": tot / wall / 1e9, "unit": "GNUPS"}, "offered_node_updates": tot,
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "max": float(lat.max())},
-            "queueing_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+            "latency_s": lat_all, "queueing_s": queue_all,
             "completed": len(res), "wall_s": wall, "peak_resident": st["peak_resident"],
+            "least_work_first_32_slots": {"aggregate": {"value": tot / wall2 / 1e9, "unit": "GNUPS"},
+                                          "latency_s": lat_sm, "queueing_s": queue_sm, "completed": len(res2),
+                                          "wall_s": wall2},
             "same_subset": {"requests": "every 4th request, all submitted at once",
                             "served": {"value": sub_nu / served_s / 1e9, "unit": "GNUPS"},
                             "plain_one_context_per_request": {"value": sub_nu / plain_s / 1e9, "unit": "GNUPS"},

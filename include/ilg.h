@@ -195,6 +195,11 @@ typedef struct {
   double t_done;
 } ilg_result;
 typedef struct ilg_server ilg_server;
+/* Admission order: arrival order (the default), or least work (Lx*Ly*steps) first —
+ * shorter requests then finish sooner; with an endless stream above capacity a large
+ * request may wait indefinitely. */
+enum { ILG_ADMIT_FIFO = 0, ILG_ADMIT_SMALLEST = 1 };
+ilg_status ilg_server_set_policy(ilg_server* s, int32_t policy);
 ilg_status ilg_server_create(uint64_t seed, uint64_t hbm_bytes, uint32_t max_slots, uint32_t quantum, void* stream,
                              ilg_server** out);
 ilg_status ilg_server_submit(ilg_server* s, uint64_t id, const ilg_params* params, uint32_t steps,

@@ -88,6 +88,7 @@ _lib.ilg_server_wait_idle.argtypes = [_vp, ctypes.c_double]
 _lib.ilg_server_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_uint32)]
 _lib.ilg_server_destroy.argtypes = [_vp]
+_lib.ilg_server_set_policy.argtypes = [_vp, ctypes.c_int32]
 _lib.ilg_server_last_error.argtypes = [_vp]
 _lib.ilg_server_last_error.restype = ctypes.c_char_p
 _lib.ilg_philox.argtypes = [_u32p, ctypes.c_uint64, _u32p, ctypes.c_size_t, _vp]
@@ -99,7 +100,7 @@ for _f in ("ilg_set_temporal_blocking", "ilg_create", "ilg_destroy", "ilg_init",
            "ilg_alias_table", "ilg_poisson_table", "ilg_observables_noalloc", "ilg_batch_create", "ilg_batch_destroy",
            "ilg_batch_init", "ilg_batch_set_state", "ilg_batch_get_state", "ilg_batch_run", "ilg_batch_observables",
            "ilg_server_create", "ilg_server_submit", "ilg_server_poll", "ilg_server_wait_idle", "ilg_server_stats",
-           "ilg_server_destroy"):
+           "ilg_server_destroy", "ilg_server_set_policy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -287,6 +288,9 @@ class Server:
     def _check(self, st):
         if st != ILG_OK:
             raise IlgError(st, _lib.ilg_server_last_error(self._h).decode(errors="replace"))
+
+    def set_policy(self, smallest_first: bool):
+        self._check(_lib.ilg_server_set_policy(self._h, 1 if smallest_first else 0))
 
     def submit(self, rid, steps, want_state=False, **params):
         p = make_params(**params)

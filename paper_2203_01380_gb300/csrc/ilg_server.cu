@@ -105,6 +105,7 @@ uint32_t mode_of(uint64_t P) {
 struct ilg_server {
   uint64_t seed = 0;
   uint32_t max_slots = 0, quantum = 0;
+  int32_t policy = ILG_ADMIT_FIFO;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int sms = 0;
@@ -293,10 +294,23 @@ void worker_main(ilg_server* s) {
     // admission: in arrival order while slots and arena memory allow
     for (;;) {
       Request rq;
+      size_t pick = 0;
       {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->pending.empty() || s->resident.size() >= s->max_slots) break;
-        rq = s->pending.front();
+        if (s->policy == ILG_ADMIT_SMALLEST) {
+          // least work (node updates) first
+          double best = -1.0;
+          for (size_t k = 0; k < s->pending.size(); ++k) {
+            const Request& q = s->pending[k];
+            const double w = double(q.p.Lx) * q.p.Ly * q.steps;
+            if (best < 0.0 || w < best) {
+              best = w;
+              pick = k;
+            }
+          }
+        }
+        rq = s->pending[pick];
       }
       Resident r;
       std::string msg;
@@ -306,7 +320,7 @@ void worker_main(ilg_server* s) {
       }
       r.t_admit = now_s(s->t0);
       std::lock_guard<std::mutex> lk(s->mu);
-      s->pending.pop_front();
+      s->pending.erase(s->pending.begin() + long(pick));
       s->resident.push_back(r);
       s->peak_resident = std::max<uint32_t>(s->peak_resident, uint32_t(s->resident.size()));
     }
@@ -502,6 +516,13 @@ ilg_status ilg_server_submit(ilg_server* s, uint64_t id, const ilg_params* p, ui
   s->pending.push_back(Request{id, *p, steps, final_state, now_s(s->t0)});
   ++s->in_flight;
   s->cv.notify_one();
+  return ILG_OK;
+}
+
+ilg_status ilg_server_set_policy(ilg_server* s, int32_t policy) {
+  if (!s || (policy != ILG_ADMIT_FIFO && policy != ILG_ADMIT_SMALLEST)) return ILG_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->policy = policy;
   return ILG_OK;
 }
 

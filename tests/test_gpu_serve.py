@@ -103,3 +103,21 @@ def test_invalid_request_and_bounded_wait(B):
         srv.wait_idle(600)
         res = {r["id"]: r for r in srv.poll()}
     assert res[2]["status"] == B.ILG_E_INVALID and res[3]["status"] == 0 and res[3]["t"] == 60000
+
+
+def test_least_work_first_admission(B):
+    """With one slot and least-work-first admission, the requests queued behind a
+    long first request are admitted smallest first; results are unchanged."""
+    reqs = requests(6, seed=13)
+    blocker = dict(lattice=2, Lx=512, Ly=512, n0=10.0, omega_eff=1.5, seed=SEED, replica=999)
+    with B.Server(SEED, 1 << 30, max_slots=1, quantum=8) as srv:
+        srv.set_policy(True)
+        srv.submit(999, steps=400, **blocker)
+        for i, r in enumerate(reqs):
+            srv.submit(1000 + i, want_state=True, **r)
+        srv.wait_idle(300)
+        results = [r for r in srv.poll() if r["id"] != 999]
+    check(B, reqs, results)
+    order = sorted(results, key=lambda r: r["t_admit"])
+    work = [reqs[r["id"] - 1000]["Lx"] * reqs[r["id"] - 1000]["Ly"] * reqs[r["id"] - 1000]["steps"] for r in order]
+    assert work == sorted(work)
