@@ -254,3 +254,51 @@ def test_large_d2q5_light_cone_full_size(B):
     win = ref.window(x0, y0, w, w, steps)
     xs = [(x0 + i) % 16384 for i in range(w)]
     assert np.array_equal(state[:, y0:y0 + w][:, :, xs], win)
+
+
+# ---------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("lattice,Lx,Ly,steps", [(2, 3, 3, 7), (2, 16, 3, 9), (2, 65536, 3, 3), (2, 8, 2051, 4),
+                                                 (1, 3, 1, 15), (1, 65544, 1, 5)])
+def test_extreme_shapes(B, lattice, Lx, Ly, steps):
+    Q = 3 if lattice == 1 else 5
+    s0 = inputs.random_state(Q, Ly, Lx, 20.0, seed=Lx % 1000 + Ly)
+    cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, omega_eff=1.55, seed=0xFFFFFFFF00000001, replica=0xFFFFFFFF)
+    got = gpu_run(B, cfg, steps, state=s0, t0=3)
+    assert np.array_equal(got, O.Lattice(**cfg).run(s0, 3, steps))
+
+
+def test_occupations_near_the_limit(B):
+    """Nodes holding up to 65535 particles in total never overflow (mass is
+    conserved per node); pure flip moves them untouched."""
+    Lx, Ly = 40, 24
+    s = np.zeros((5, Ly, Lx), np.uint16)
+    s[0, 3, 5] = 65535
+    s[1, 10, 10] = 30000
+    s[2, 10, 10] = 35535
+    s[:, 20, 30] = [13107] * 5
+    for omega in (0.5, 1.0, 1.5, 2.0):
+        cfg = dict(lattice=2, Lx=Lx, Ly=Ly, omega_eff=omega, seed=77)
+        got = gpu_run(B, cfg, 6, state=s, t0=0)
+        assert np.array_equal(got, O.Lattice(**cfg).run(s, 0, 6)), omega
+
+
+def test_step_counter_limit(B):
+    s0 = inputs.random_state(3, 1, 32, 10.0, seed=1)
+    cfg = dict(lattice=1, Lx=32, omega_eff=1.2, seed=2)
+    t0 = (1 << 32) - 20
+    got = gpu_run(B, cfg, 10, state=s0, t0=t0)
+    assert np.array_equal(got, O.Lattice(**cfg).run(s0, t0, 10))
+    with B.Lattice(**cfg) as lat:
+        lat.set_state(s0, t0)
+        with pytest.raises(B.IlgError) as e:
+            lat.step(20)
+        assert e.value.status == B.ILG_E_INVALID
+
+
+def test_init_largest_mean(B):
+    cfg = dict(lattice=2, Lx=64, Ly=16, n0=660.0, amp=150.0, mode_mx=2, init_weighted=0, seed=6)
+    with B.Lattice(**cfg) as lat:
+        lat.init()
+        got, _ = lat.get_state()
+    assert np.array_equal(got, O.Lattice(**cfg).init())
