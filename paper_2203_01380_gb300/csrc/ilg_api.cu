@@ -36,6 +36,8 @@ struct ilg_ctx {
   double* d_res = nullptr;
   uint32_t mode_cap = 0;
   uint32_t tb_depth = 0;                   // temporal blocking: steps per launch (0: off)
+  uint32_t general = 0;                    // high occupation: general collision path at once
+  double omega_star = 0;
   unsigned long long* h_word = nullptr;    // pinned 8-byte readback
   std::string err;
 };
@@ -103,9 +105,10 @@ void round_keys(uint64_t seed, uint32_t* rk) {
 namespace {
 using ilg::validate_params;
 
-int step_grid(const ilg_ctx* c) {
+// node-parallel kernels: `per_sm` resident blocks of 256 threads on every SM
+int step_grid(const ilg_ctx* c, size_t per_sm = 4) {
   const size_t blocks = (c->nodes + 255) / 256;
-  const size_t cap = size_t(c->sms) * 4;
+  const size_t cap = size_t(c->sms) * per_sm;
   return int(blocks < cap ? blocks : cap);
 }
 
@@ -123,6 +126,7 @@ StepArgs step_args(const ilg_ctx* c) {
   a.flip = c->flip;
   a.omega_mode = prob_mode(c->P_omega);
   a.rest_mode = prob_mode(c->P_rest);
+  a.general = c->general;
   a.key0 = uint32_t(c->p.seed);
   a.key1 = uint32_t(c->p.seed >> 32);
   a.replica = c->p.replica;
@@ -176,6 +180,7 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
     c->flip = 1;
     omega_star = 2.0 - c->p.omega_eff;
   }
+  c->omega_star = omega_star;
   c->P_omega = quantise_probability(omega_star);
   c->P_rest = quantise_probability(w[0]);
   c->nodes = size_t(c->p.Lx) * c->p.Ly;
@@ -280,6 +285,20 @@ ilg_status ilg_init(ilg_ctx* c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   c->t = 0;
   c->has_state = true;
+  c->general = general_path(c->Q, c->omega_star, c->p.n0);
+  return ILG_OK;
+}
+
+// mean occupation of the current state decides between the collision paths
+static ilg_status update_path_choice(ilg_ctx* c) {
+  const uint32_t Lx = c->p.Lx, Ly = c->p.Ly;
+  ILG_CUDA(c, cudaMemsetAsync(c->d_col, 0, sizeof(unsigned long long) * Lx, c->stream), "clear sums");
+  ILG_CUDA(c, launch_sums(c->Q, c->buf[c->cur], Lx, Ly, c->d_col, c->d_row, 0, c->stream), "sums kernel");
+  ILG_CUDA(c, launch_project(c->d_col, c->d_row, Lx, Ly, nullptr, 0, nullptr, c->d_mass, c->stream), "mass kernel");
+  ILG_CUDA(c, cudaMemcpyAsync(c->h_word, c->d_mass, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
+           "read mass");
+  ILG_CUDA(c, cudaStreamSynchronize(c->stream), "read mass");
+  c->general = general_path(c->Q, c->omega_star, double(*c->h_word) / (double(c->nodes) * c->Q));
   return ILG_OK;
 }
 
@@ -291,7 +310,7 @@ static ilg_status set_state_impl(ilg_ctx* c, const uint16_t* src, size_t n, uint
   ILG_CUDA(c, cudaStreamSynchronize(c->stream), "copy state in");
   c->t = t;
   c->has_state = true;
-  return ILG_OK;
+  return update_path_choice(c);
 }
 
 static ilg_status get_state_impl(ilg_ctx* c, uint16_t* dst, size_t n, uint64_t* t, cudaMemcpyKind kind) {
@@ -332,8 +351,9 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   if (c->t + T >= (uint64_t(1) << 32)) return fail(c, ILG_E_INVALID, "step counter would reach 2^32");
   if (T == 0) return ILG_OK;
   const StepArgs a = step_args(c);
-  const bool vec = (c->p.Lx % step_vec_width()) == 0;
-  const int grid = vec ? vec_grid(c) : step_grid(c);
+  // high occupations go straight to the general collision (node-parallel kernel)
+  const bool vec = !c->general && (c->p.Lx % step_vec_width()) == 0;
+  const int grid = vec ? vec_grid(c) : step_grid(c, 3);
   const int cur0 = c->cur;
   const uint64_t t0 = c->t;
   // launches: blocks of tb_depth steps (temporal blocking), then single steps;

@@ -55,7 +55,8 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, StepArgs common) {
   extern __shared__ uint4 smem4[];
   uint32_t* tables = reinterpret_cast<uint32_t*>(smem4);                     // kDevBlockWords words
-  uint16_t* ring = reinterpret_cast<uint16_t*>(tables + kDevBlockWords);      // 2 x 3 x Lmax
+  uint32_t* xbuf = tables + kDevBlockWords;                                   // kBatchExtWords x THREADS
+  uint16_t* ring = reinterpret_cast<uint16_t*>(xbuf + kBatchExtWords * THREADS);  // 2 x 3 x Lmax
   __shared__ uint32_t s_task;
   __shared__ int s_fail;
   __shared__ unsigned long long s_mass;
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, Ste
     a.omega_mode = d.omega_mode;
     a.rest_mode = d.rest_mode;
     a.replica = d.replica;
+    a.general = d.general;
 
     // tables and ring into shared memory
     const uint4* gt = reinterpret_cast<const uint4*>(b.tables + size_t(r) * kDevBlockWords);
@@ -116,8 +118,8 @@ __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, Ste
         m[0] = n[0];
         m[1] = a.flip ? n[2] : n[1];
         m[2] = a.flip ? n[1] : n[2];
-        if (!collide_try_fast<3>(a, tables, x, t, m, post)) {
-          collide<3>(a, tables, x, t, m, post);
+        if (a.general || !collide_try_fast<3>(a, tables, x, t, m, post)) {
+          collide_phased<3, kBatchExtWords, THREADS>(a, tables, x, t, m, post, xbuf + tid);
           bad |= post[0] > 65535u || post[1] > 65535u || post[2] > 65535u;
         }
         const uint32_t xp = x + 1 == L ? 0 : x + 1;
@@ -169,7 +171,8 @@ __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, Ste
 constexpr int kBatchThreads = 1024;
 
 size_t batch_smem_bytes(uint32_t Lmax) {
-  return sizeof(uint32_t) * kDevBlockWords + sizeof(uint16_t) * 2 * 3 * size_t(Lmax);
+  return sizeof(uint32_t) * (kDevBlockWords + size_t(kBatchExtWords) * kBatchThreads) +
+         sizeof(uint16_t) * 2 * 3 * size_t(Lmax);
 }
 
 cudaError_t prepare_batch_kernel(uint32_t Lmax) {

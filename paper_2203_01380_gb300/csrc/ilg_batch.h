@@ -10,7 +10,8 @@
 
 namespace ilg {
 
-constexpr uint32_t kBatchMaxL = 16384;  // longest ring (the ring and its copy live in shared memory)
+constexpr uint32_t kBatchMaxL = 10240;  // longest ring (the ring and its copy live in shared memory)
+constexpr int kBatchExtWords = 16;      // extension words per thread in shared memory
 
 struct ReplicaDesc {
   uint32_t L;           // ring length
@@ -19,6 +20,8 @@ struct ReplicaDesc {
   uint32_t rest_mode;
   uint32_t replica;     // replica word of the Philox counter
   uint32_t t;           // step counter (advanced by the kernel)
+  uint32_t general;     // 1: skip the fast path (high occupation)
+  uint32_t pad;
   uint64_t state_off;   // first of the replica's 3 L occupations in the batch buffer
 };
 

@@ -99,7 +99,7 @@ ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, 
     if (!bad.empty()) return bfail(nullptr, ILG_E_INVALID, "replica " + std::to_string(i) + ": " + bad);
     if (params[i].lattice != ILG_D1Q3) return bfail(nullptr, ILG_E_INVALID, "batches hold D1Q3 rings");
     if (params[i].seed != params[0].seed) return bfail(nullptr, ILG_E_INVALID, "all replicas of a batch share one seed");
-    if (params[i].Lx > kBatchMaxL) return bfail(nullptr, ILG_E_INVALID, "ring longer than 16384");
+    if (params[i].Lx > kBatchMaxL) return bfail(nullptr, ILG_E_INVALID, "ring longer than 10240");
   }
   ilg_batch* b = new (std::nothrow) ilg_batch();
   if (!b) return bfail(nullptr, ILG_E_OOM, "host allocation failed");
@@ -135,6 +135,7 @@ ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, 
     d.rest_mode = mode_of(Pr);
     d.replica = q.replica;
     d.t = 0;
+    d.general = general_path(3, omega_star, q.n0);
     d.state_off = b->total;
     b->total += 3 * size_t(q.Lx);
     b->Lmax = std::max(b->Lmax, q.Lx);
@@ -228,6 +229,10 @@ ilg_status ilg_batch_set_state(ilg_batch* b, uint32_t i, const uint16_t* host, s
   if (n != 3 * size_t(b->desc[i].L)) return bfail(b, ILG_E_INVALID, "state size must be 3 * L");
   if (t >= (uint64_t(1) << 32)) return bfail(b, ILG_E_INVALID, "t must be below 2^32");
   b->desc[i].t = uint32_t(t);
+  uint64_t mass = 0;
+  for (size_t k = 0; k < n; ++k) mass += host[k];
+  const double om = b->p[i].omega_eff > 1.0 ? 2.0 - b->p[i].omega_eff : b->p[i].omega_eff;
+  b->desc[i].general = general_path(3, om, double(mass) / double(n));
   BCUDA(b, cudaMemcpyAsync(b->d_state + b->desc[i].state_off, host, sizeof(uint16_t) * n, cudaMemcpyHostToDevice, b->stream),
         "copy state in");
   BCUDA(b, cudaMemcpyAsync(b->d_desc + i, &b->desc[i], sizeof(ReplicaDesc), cudaMemcpyHostToDevice, b->stream), "copy desc");

@@ -14,6 +14,7 @@ constexpr uint32_t kDevBlockWords = 2 * kDevAliasEntries * 2;
 constexpr uint32_t kDevTagStep = 1u << 24;
 constexpr uint32_t kDevTagExt = 2u << 24;
 constexpr uint32_t kDevTagInit = 3u << 24;
+constexpr int kExtWords = 24;        // extension words per thread held in shared memory
 
 // How a probability P/2^32 is drawn: never (P = 0), by table (0 < P < 2^32),
 // always (P = 2^32).
@@ -24,6 +25,7 @@ struct StepArgs {
   uint32_t flip;
   uint32_t omega_mode;   // kNever / kTable / kAlways for the thinning probability
   uint32_t rest_mode;    // same for the rest weight w_0
+  uint32_t general;      // 1: occupations so high that the fast path would mostly fail
   uint32_t key0, key1;   // Philox key = seed
   uint32_t replica;
   const uint32_t* tables;   // device, kDevBlockWords words (layout above)
@@ -152,6 +154,120 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* s, ui
       out[2] += __popc(~ax & sg & mask);
       out[3] += __popc(ax & ~sg & mask);
       out[4] += __popc(ax & sg & mask);
+    }
+    moving -= c;
+    first = false;
+  }
+}
+
+// Extension words held in shared memory: this thread's buffer holds words
+// [base, base + K) of its extension stream, word e at xb[(e - base) * S] (threads
+// interleaved with stride S, so a warp's accesses hit distinct banks).  Blocks are
+// generated in order, a phase at a time; a word past the buffer refills it with
+// the next K words.  Same stream, same bits as the lazy reader.
+template <int K, int S>
+struct ExtBuffer {
+  static_assert(K % 4 == 0, "whole Philox blocks");
+  uint32_t* xb;
+  uint32_t base;    // first word held (a multiple of 4)
+  uint32_t filled;  // words generated so far (base <= filled <= base + K)
+  uint32_t next;    // words consumed so far
+
+  __device__ __forceinline__ void fill(const StepArgs& a, uint32_t node, uint32_t t, uint32_t upto) {
+    upto = upto < base + uint32_t(K) ? upto : base + uint32_t(K);
+    while (filled < upto) {
+      const uint4 b = philox_rk(make_uint4(node, t, a.replica, kDevTagExt | (filled >> 2)), a.rk);
+      uint32_t* p = xb + (filled - base) * S;
+      p[0] = b.x;
+      p[S] = b.y;
+      p[2 * S] = b.z;
+      p[3 * S] = b.w;
+      filled += 4;
+    }
+  }
+  __device__ __forceinline__ uint32_t take(const StepArgs& a, uint32_t node, uint32_t t) {
+    const uint32_t e = next++;
+    if (e >= filled) {
+      if (e >= base + uint32_t(K)) {
+        base = e & ~3u;
+        filled = base;
+      }
+      fill(a, node, t, base + uint32_t(K));
+    }
+    return xb[(e - base) * S];
+  }
+};
+
+// Binomial(m, P) with the chunks beyond the first drawn from the buffer.
+template <int K, int S>
+__device__ __forceinline__ uint32_t binomial_buf(uint32_t mode, const uint2* A, uint32_t m, uint32_t slot,
+                                                 const StepArgs& a, uint32_t node, uint32_t t,
+                                                 ExtBuffer<K, S>& eb) {
+  if (mode == kNever || m == 0) return 0;
+  if (mode == kAlways) return m;
+  uint32_t r = binomial_alias(A, m < kDevNmax ? m : kDevNmax, slot);
+  for (uint32_t left = m > kDevNmax ? m - kDevNmax : 0; left > 0;) {
+    const uint32_t c = left < kDevNmax ? left : kDevNmax;
+    r += binomial_alias(A, c, eb.take(a, node, t));
+    left -= c;
+  }
+  return r;
+}
+
+__device__ __forceinline__ uint32_t extra_chunks(uint32_t mode, uint32_t m) {
+  return (mode == kTable && m > kDevNmax) ? (m - 1) / kDevNmax : 0u;
+}
+
+// The general collision, phase by phase: the extension words each phase needs
+// (thinning chunks, rest chunks, moving groups) are generated together, once,
+// before the phase, so a warp runs the Philox blocks in one place.  Same words,
+// same order and same result as collide().
+template <int Q, int K, int S>
+__device__ __forceinline__ void collide_phased(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
+                                               const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
+  const uint2* to = thinning_table(s);
+  const uint2* tr = rest_table(s);
+  const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
+  const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
+  const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  ExtBuffer<K, S> eb{xb, 0u, 0u, 0u};
+
+  uint32_t need = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) need += extra_chunks(a.omega_mode, m[i]);
+  eb.fill(a, node, t, need);
+  uint32_t removed = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const uint32_t r = binomial_buf<K, S>(a.omega_mode, to, m[i], W[i], a, node, t, eb);
+    out[i] = m[i] - r;
+    removed += r;
+  }
+  need += extra_chunks(a.rest_mode, removed);
+  eb.fill(a, node, t, need);
+  const uint32_t to_rest = binomial_buf<K, S>(a.rest_mode, tr, removed, W[Q], a, node, t, eb);
+  out[0] += to_rest;
+  uint32_t moving = removed - to_rest;
+  const uint32_t groups = (moving + 31) / 32;
+  need += (groups > 1 ? groups - 1 : 0) * (Q == 5 ? 2u : 1u);
+  eb.fill(a, node, t, need);
+  bool first = true;
+  while (moving > 0) {
+    const uint32_t c = moving < 32 ? moving : 32;
+    const uint32_t mask = c == 32 ? 0xFFFFFFFFu : ((1u << c) - 1u);
+    if constexpr (Q == 3) {
+      const uint32_t sw = first ? W[Q + 1] : eb.take(a, node, t);
+      const uint32_t minus = __popc(sw & mask);
+      out[1] += c - minus;
+      out[2] += minus;
+    } else {
+      const uint32_t ax = (first ? W[Q + 1] : eb.take(a, node, t)) & mask;
+      const uint32_t sg = (first ? W[Q + 2] : eb.take(a, node, t)) & mask;
+      const uint32_t ny = __popc(ax), nmy = __popc(ax & sg), nmx = __popc(sg & ~ax);
+      out[1] += c - ny - nmx;
+      out[2] += nmx;
+      out[3] += ny - nmy;
+      out[4] += nmy;
     }
     moving -= c;
     first = false;

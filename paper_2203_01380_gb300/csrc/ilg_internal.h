@@ -33,6 +33,7 @@ void build_binomial_table(uint64_t P, uint32_t* T);
 void build_alias_table(uint64_t P, AliasEntry* out);
 uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap);
 uint64_t quantise_probability(double p);
+uint32_t general_path(int Q, double omega_star, double mean_occupation);
 void weights(int lattice, double theta, double* w);
 
 // Poisson tables of the initial state, one per (velocity class, phase residue).

@@ -15,13 +15,16 @@ namespace ilg {
 // block.  A block returns without work when an earlier launch recorded an
 // overflow.
 // --------------------------------------------------------------------------
+constexpr int kStepThreads = 256;
+
 template <int Q>
-__global__ void __launch_bounds__(256, 4) step_kernel(StepArgs a, const uint16_t* __restrict__ in,
+__global__ void __launch_bounds__(kStepThreads, 3) step_kernel(StepArgs a, const uint16_t* __restrict__ in,
                                                       uint16_t* __restrict__ out, uint32_t t,
                                                       unsigned long long* __restrict__ fail) {
   extern __shared__ uint4 smem4[];
   __shared__ int skip;
   uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
+  uint32_t* xb = s + kDevBlockWords + threadIdx.x;  // this thread's extension words
   if (threadIdx.x == 0) skip = (*reinterpret_cast<volatile unsigned long long*>(fail) != ~0ull);
   const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
   for (uint32_t i = threadIdx.x; i < kDevBlockWords / 4; i += blockDim.x) smem4[i] = g4[i];
@@ -49,8 +52,8 @@ __global__ void __launch_bounds__(256, 4) step_kernel(StepArgs a, const uint16_t
       m[3] = a.flip ? n[4] : n[3];
       m[4] = a.flip ? n[3] : n[4];
     }
-    if (!collide_try_fast<Q>(a, s, node, t, m, post)) {
-      collide<Q>(a, s, node, t, m, post);
+    if (a.general || !collide_try_fast<Q>(a, s, node, t, m, post)) {
+      collide_phased<Q, kExtWords, kStepThreads>(a, s, node, t, m, post, xb);
 #pragma unroll
       for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
     }
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(256, 4) step_kernel(StepArgs a, const uint16_t
   if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
 }
 
-constexpr size_t kStepSmem = sizeof(uint32_t) * kDevBlockWords;
+constexpr size_t kStepSmem = sizeof(uint32_t) * (kDevBlockWords + kExtWords * kStepThreads);
 
 cudaError_t prepare_step_kernels() {
   cudaError_t e = cudaFuncSetAttribute(step_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStepSmem));
@@ -80,8 +83,8 @@ cudaError_t prepare_step_kernels() {
 
 cudaError_t launch_step(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                         unsigned long long* fail, int grid, cudaStream_t s) {
-  if (Q == 3) step_kernel<3><<<grid, 256, kStepSmem, s>>>(a, in, out, t, fail);
-  else step_kernel<5><<<grid, 256, kStepSmem, s>>>(a, in, out, t, fail);
+  if (Q == 3) step_kernel<3><<<grid, kStepThreads, kStepSmem, s>>>(a, in, out, t, fail);
+  else step_kernel<5><<<grid, kStepThreads, kStepSmem, s>>>(a, in, out, t, fail);
   return cudaGetLastError();
 }
 

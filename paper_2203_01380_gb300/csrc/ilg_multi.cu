@@ -20,7 +20,7 @@ namespace {
 template <int Q>
 __device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s, const uint16_t* __restrict__ in,
                                            uint16_t* __restrict__ out, uint32_t node0, uint32_t node1, uint32_t t,
-                                           bool& bad) {
+                                           bool& bad, uint32_t* xb) {
   const uint32_t Lx = a.Lx, Ly = a.Ly;
   const size_t plane = size_t(Lx) * Ly;
   for (uint32_t nd = node0 + threadIdx.x; nd < node1; nd += blockDim.x) {
@@ -38,8 +38,8 @@ __device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s,
       m[3] = a.flip ? n[4] : n[3];
       m[4] = a.flip ? n[3] : n[4];
     }
-    if (!collide_try_fast<Q>(a, s, uint32_t(at), t, m, post)) {
-      collide<Q>(a, s, uint32_t(at), t, m, post);
+    if (a.general || !collide_try_fast<Q>(a, s, uint32_t(at), t, m, post)) {
+      collide_phased<Q, kExtWords, kMultiThreads>(a, s, uint32_t(at), t, m, post, xb);
 #pragma unroll
       for (int k = 0; k < Q; ++k) bad |= post[k] > 65535u;
     }
@@ -58,7 +58,7 @@ __device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s,
 }
 
 template <int Q>
-__global__ void __launch_bounds__(kMultiThreads, 4) multi_step_kernel(MultiArgs ma, StepArgs common,
+__global__ void __launch_bounds__(kMultiThreads, 3) multi_step_kernel(MultiArgs ma, StepArgs common,
                                                                       uint32_t sub) {
   extern __shared__ uint4 smem4[];
   uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
@@ -91,12 +91,13 @@ __global__ void __launch_bounds__(kMultiThreads, 4) multi_step_kernel(MultiArgs 
     a.omega_mode = d.omega_mode;
     a.rest_mode = d.rest_mode;
     a.replica = d.replica;
+    a.general = d.general;
     const uint32_t t = d.t0 + sub;
     const bool odd = ((sub + d.phase) & 1u) != 0;
     const uint16_t* in = odd ? d.buf1 : d.buf0;
     uint16_t* out = odd ? d.buf0 : d.buf1;
     bool bad = false;
-    step_nodes<Q>(a, s, in, out, w.node0, w.node1, t, bad);
+    step_nodes<Q>(a, s, in, out, w.node0, w.node1, t, bad, s + kDevBlockWords + threadIdx.x);
     if (bad) atomicMin(ma.fail + w.lattice, sub);
     __syncthreads();  // the tables and s_item stay in use until every thread is done
   }
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kMultiThreads, 4) multi_step_kernel(MultiArgs 
 
 }  // namespace
 
-size_t multi_smem_bytes() { return sizeof(uint32_t) * kDevBlockWords; }
+size_t multi_smem_bytes() { return sizeof(uint32_t) * (kDevBlockWords + kExtWords * kMultiThreads); }
 
 cudaError_t prepare_multi_kernel() {
   return cudaFuncSetAttribute(multi_step_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,

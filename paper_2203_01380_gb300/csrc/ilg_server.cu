@@ -44,7 +44,7 @@ struct Resident {
   size_t off_state = 0, state_bytes = 0;  // two buffers
   size_t off_tab = 0;
   uint32_t t = 0, remaining = 0, phase = 0;
-  uint32_t flip = 0, omega_mode = 0, rest_mode = 0;
+  uint32_t flip = 0, omega_mode = 0, rest_mode = 0, general = 0;
   double t_admit = 0;
   int status = ILG_OK;
 };
@@ -190,6 +190,7 @@ bool admit(ilg_server* s, const Request& rq, Resident* out, cudaError_t* cerr, s
   const double omega_star = rq.p.omega_eff > 1.0 ? 2.0 - rq.p.omega_eff : rq.p.omega_eff;
   const uint64_t Po = quantise_probability(omega_star), Pr = quantise_probability(w[0]);
   r.flip = rq.p.omega_eff > 1.0 ? 1u : 0u;
+  r.general = general_path(5, omega_star, rq.p.n0);
   r.omega_mode = mode_of(Po);
   r.rest_mode = mode_of(Pr);
   std::vector<uint32_t> tables(kBlockWords, 0u);
@@ -346,6 +347,7 @@ void worker_main(ilg_server* s) {
       d.omega_mode = r.omega_mode;
       d.rest_mode = r.rest_mode;
       d.steps = std::min(q, r.remaining);
+      d.general = r.general;
       d.buf0 = reinterpret_cast<uint16_t*>(s->d_arena + r.off_state);
       d.buf1 = reinterpret_cast<uint16_t*>(s->d_arena + r.off_state + r.state_bytes);
       d.tables = reinterpret_cast<const uint32_t*>(s->d_arena + r.off_tab);

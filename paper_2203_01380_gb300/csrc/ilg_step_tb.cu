@@ -18,6 +18,7 @@ namespace ilg {
 namespace {
 
 constexpr int kTbThreads = 256;
+constexpr int kTbExtWords = 8;
 
 __global__ void __launch_bounds__(kTbThreads, 2) step_tb_kernel(StepArgs a, const uint16_t* __restrict__ in,
                                                                 uint16_t* __restrict__ out, uint32_t t0,
@@ -27,7 +28,8 @@ __global__ void __launch_bounds__(kTbThreads, 2) step_tb_kernel(StepArgs a, cons
   uint32_t* tables = reinterpret_cast<uint32_t*>(smem4);
   const uint32_t W = B + 2 * Tb;
   const uint32_t area = W * W;
-  uint16_t* bufA = reinterpret_cast<uint16_t*>(tables + kDevBlockWords);
+  uint32_t* xbuf = tables + kDevBlockWords;  // kTbExtWords per thread, interleaved
+  uint16_t* bufA = reinterpret_cast<uint16_t*>(xbuf + kTbExtWords * kTbThreads);
   uint16_t* bufB = bufA + 5 * area;
   __shared__ int skip;
   const uint32_t Lx = a.Lx, Ly = a.Ly;
@@ -71,8 +73,8 @@ __global__ void __launch_bounds__(kTbThreads, 2) step_tb_kernel(StepArgs a, cons
         m[2] = a.flip ? n[1] : n[2];
         m[3] = a.flip ? n[4] : n[3];
         m[4] = a.flip ? n[3] : n[4];
-        if (!collide_try_fast<5>(a, tables, node, t0 + k, m, post)) {
-          collide<5>(a, tables, node, t0 + k, m, post);
+        if (a.general || !collide_try_fast<5>(a, tables, node, t0 + k, m, post)) {
+          collide_phased<5, kTbExtWords, kTbThreads>(a, tables, node, t0 + k, m, post, xbuf + threadIdx.x);
 #pragma unroll
           for (int i = 0; i < 5; ++i) bad |= post[i] > 65535u;
         }
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(kTbThreads, 2) step_tb_kernel(StepArgs a, cons
 
 size_t step_tb_smem_bytes(uint32_t B, uint32_t Tb) {
   const size_t W = B + 2 * Tb;
-  return sizeof(uint32_t) * kDevBlockWords + 2 * 5 * W * W * sizeof(uint16_t);
+  return sizeof(uint32_t) * (kDevBlockWords + kTbExtWords * kTbThreads) + 2 * 5 * W * W * sizeof(uint16_t);
 }
 
 cudaError_t prepare_step_tb_kernel(uint32_t B, uint32_t Tb) {

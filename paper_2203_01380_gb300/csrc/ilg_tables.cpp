@@ -102,6 +102,14 @@ uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap) {
   return 0;
 }
 
+// The fast collision path needs at most 63 removed and 32 moving particles per
+// node; with about omega* Q m removed on average (m = mean occupation per
+// velocity), above ~40 it would mostly fail and the general path is taken at once.
+// Either path gives the same result.
+uint32_t general_path(int Q, double omega_star, double mean_occupation) {
+  return omega_star * Q * mean_occupation > 40.0 ? 1u : 0u;
+}
+
 uint64_t quantise_probability(double p) {
   double v = std::floor(p * 4294967296.0 + 0.5);
   if (v <= 0.0) return 0;

@@ -302,3 +302,28 @@ def test_init_largest_mean(B):
         lat.init()
         got, _ = lat.get_state()
     assert np.array_equal(got, O.Lattice(**cfg).init())
+
+
+@pytest.mark.parametrize("lattice,Lx,Ly,n0,omega", [(2, 64, 16, 660.0, 1.0), (1, 512, 1, 660.0, 1.0),
+                                                    (2, 40, 24, 120.0, 1.5), (1, 96, 1, 300.0, 0.6)])
+def test_step_very_high_occupation(B, lattice, Lx, Ly, n0, omega):
+    """Hundreds of particles per velocity: the general collision needs more
+    extension words than a thread's shared-memory buffer holds and refills it."""
+    cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, n0=n0, amp=n0 / 20, mode_mx=1, init_weighted=0,
+               omega_eff=omega, seed=31, replica=4)
+    ref = O.Lattice(**cfg)
+    assert np.array_equal(gpu_run(B, cfg, 6), ref.run(ref.init(), 0, 6))
+
+
+def test_set_state_high_mass_takes_general_path(B):
+    """A state set from the host with a high mean (decided on the device) after an
+    init with a low one: same bits as the oracle either way."""
+    cfg = dict(lattice=2, Lx=64, Ly=32, n0=5.0, omega_eff=1.2, seed=8)
+    s_hi = inputs.random_state(5, 32, 64, 90.0, seed=3)
+    with B.Lattice(**cfg) as lat:
+        lat.init()
+        lat.step(3)
+        lat.set_state(s_hi, 11)
+        lat.step(5)
+        got, t = lat.get_state()
+    assert t == 16 and np.array_equal(got, O.Lattice(**cfg).run(s_hi, 11, 5))

@@ -29,6 +29,21 @@ def test_tb_equals_single_steps_and_oracle(B, Lx, Ly, depth, steps):
     assert np.array_equal(got, O.Lattice(**cfg).run(s0, 40, steps))
 
 
+def test_tb_high_occupation(B):
+    """Mean occupation 60 per velocity: every node takes the general collision,
+    with more extension words than the per-thread buffer holds."""
+    Lx, Ly = 70, 52
+    cfg = dict(lattice=2, Lx=Lx, Ly=Ly, n0=60.0, amp=25.0, mode_mx=1, omega_eff=1.0, seed=21, replica=5)
+    ref = O.Lattice(**cfg)
+    s0 = ref.init()
+    with B.Lattice(**cfg) as lat:
+        lat.set_temporal_blocking(3)
+        lat.init()
+        lat.step(7)
+        got, t = lat.get_state()
+    assert t == 7 and np.array_equal(got, ref.run(s0, 0, 7))
+
+
 def test_tb_full_size_window(B):
     """16384^2 workload, 40 steps at depth 4 against single steps (whole state)."""
     cfg = {k: v for k, v in inputs.LARGE_D2Q5.items() if k != "steps"}
