@@ -191,6 +191,45 @@ def measure_batched(torch, B, dev):
             "speedup_vs_plain": v / vp}
 
 
+FP64_LANES_PER_SM_CYCLE = 2.0   # GB300 nominal 1.25 TFLOP/s fp64 = 2 fused multiply-add lanes per SM per cycle at 2070 MHz
+LB_FP64_OPS_PER_NU = 15         # D2Q5: 4 adds, 2 multiplies, 9 fused multiply-adds, one fp64 lane-op each
+LB_BYTES_PER_NU = 80            # 5 doubles read + 5 written
+
+
+def measure_lb(torch, B, dev, clocks):
+    """Lattice Boltzmann comparator (Sec. IV) on the 16384^2 D2Q5 lattice, 100 steps."""
+    cfg = dict(inputs.LB_D2Q5)
+    oj, om = B.lb_rates(cfg["omega_eff"])
+    kw = {k: v for k, v in cfg.items() if k not in ("omega_eff", "steps")}
+    st = torch.cuda.Stream(dev)
+    T = 100
+    with B.LB(omega_j=oj, omega=om, stream=st, **kw) as lb:
+        lb.init()
+        lb.step(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        lb.step(T)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / T
+        mass = lb.observables()["mass"]
+    nodes = kw["Lx"] * kw["Ly"]
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = FP64_LANES_PER_SM_CYCLE * SMS * mhz * 1e6 / 1e9
+    ach = LB_FP64_OPS_PER_NU * nodes / (ms / 1e3) / 1e9
+    gbs = LB_BYTES_PER_NU * nodes / (ms / 1e3) / 1e9
+    pk = peaks()
+    hpk = pk["hbm_gbs"] if pk else 6800.0
+    return {"workload": f"lb_d2q5: D2Q5 {kw['Lx']}x{kw['Ly']} fp64, omega^j {oj}, omega {om:.2f}, {T} steps",
+            "value": nodes / (ms / 1e3) / 1e9, "unit": "GNUPS", "ms_per_step": ms,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G fp64 lane-ops/s", "frac": ach / peak,
+                         "kernel": "lb_step_kernel<5>", "fp64_ops_per_node_update": LB_FP64_OPS_PER_NU,
+                         "peak_source": "nominal 1.25 TFLOP/s fp64 (2 FMA lanes per SM per cycle) at the measured SM clock"},
+            "hbm": {"achieved": gbs, "peak": hpk, "unit": "GB/s", "frac": gbs / hpk},
+            "mass": mass}
+
+
 def serve_stream(B, reqs, slots, smallest_first):
     """Submit requests at their arrival times; returns results, wall time, stats."""
     with B.Server(5, 48 << 30, max_slots=slots, quantum=32) as srv:
@@ -390,6 +429,7 @@ def main():
         extra["temporal_blocking"] = {"steps_per_launch": tb, "single_step_kernel": {"value": value, "unit": "GNUPS"},
                                       "tile": "48 x 48 with a halo of depth nodes"}
         extra["batched"] = measure_batched(torch, B, dev)
+        extra["lattice_boltzmann"] = measure_lb(torch, B, dev, clk.summary())
         extra["serving"] = measure_serving(B)
 
     cpu = None

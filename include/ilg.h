@@ -210,6 +210,62 @@ ilg_status ilg_server_stats(ilg_server* s, double* busy_s, double* node_updates,
 ilg_status ilg_server_destroy(ilg_server* s);
 const char* ilg_server_last_error(const ilg_server* s);
 
+/* ---------------------------------------------------------------------------
+ * Lattice Boltzmann comparator: the multi-relaxation-time lattice Boltzmann
+ * equation that the lattice gas averages to (Sec. IV, Eq. MRTLB), in double
+ * precision on the same lattices:
+ *   f_i(x + v_i, t+1) = f_i^0 + sum_a w_i m_i^a (1 - omega^a) sum_j m_j^a (f_j - f_j^0),
+ *   f_i^0 = w_i rho,  rho = sum_i f_i,
+ * with m_i^a a transform matrix orthonormal under the weights (Sec. IV, Eq.
+ * transform for D1Q3), omega^j for the current (odd) moments and omega for the
+ * other non-conserved (even) moments.  The lattice gas with omega_eff > 1 has
+ * omega^j = omega_eff, omega = 2 - omega_eff (Sec. IV, Eq. omegaj); with
+ * omega_eff <= 1 both equal omega_eff.  Started from the means of the gas's
+ * Poisson initial state it gives the gas's ensemble mean at every step.
+ *
+ * Parameters: lattice, Lx, Ly, mode_mx, mode_my, init_weighted, n0, amp, theta as
+ * in ilg_params (they define the initial f = the Poisson means lambda_i(x), which
+ * must lie in [0, 700]); omega_j and omega in [0, 2].
+ * State: Q planes f[i][y][x] of doubles, same order as the gas.  The library owns
+ * the device memory (two state buffers of Q*Lx*Ly doubles); the caller owns host
+ * arrays.  Calls on one object are not thread-safe; every call returns a status,
+ * ilg_lb_last_error describes the last failure (ilg_lb_last_error(NULL): the last
+ * failed ilg_lb_create). */
+typedef struct {
+  int32_t lattice;
+  uint32_t Lx;
+  uint32_t Ly;
+  int32_t mode_mx;
+  int32_t mode_my;
+  int32_t init_weighted;
+  double n0;
+  double amp;
+  double omega_j;
+  double omega;
+  double theta;
+} ilg_lb_params;
+
+typedef struct ilg_lb ilg_lb;
+
+ilg_status ilg_lb_create(const ilg_lb_params* params, void* stream, ilg_lb** out);
+ilg_status ilg_lb_destroy(ilg_lb* lb);
+const char* ilg_lb_last_error(const ilg_lb* lb);
+/* f := lambda (the gas's Poisson means, Sec. V), t := 0. */
+ilg_status ilg_lb_init(ilg_lb* lb);
+/* Copy a state in or out (host arrays of n = Q*Lx*Ly doubles); synchronous. */
+ilg_status ilg_lb_set_state(ilg_lb* lb, const double* host, size_t n, uint64_t t);
+ilg_status ilg_lb_get_state(ilg_lb* lb, double* host, size_t n, uint64_t* t);
+/* Advance T steps, queued on the object's stream (asynchronous). */
+ilg_status ilg_lb_step(ilg_lb* lb, uint32_t T);
+/* Mass M = sum f and, per axis mode (mx, my) (at most 256), with C the column
+ * (row) sums of rho and r = (m x) mod L:
+ *   re = sum_x cos(2 pi r / L) (C(x) - M / L),  im = sum_x sin(2 pi r / L) (C(x) - M / L),
+ *   amp = im / (Lx*Ly/2)  (the measured amplitude of Sec. V).
+ * Sums in a fixed order (deterministic), compensated.  Host outputs, each may be
+ * NULL; synchronous. */
+ilg_status ilg_lb_observables(ilg_lb* lb, const int32_t* modes, uint32_t nmodes, uint64_t* t, double* mass,
+                              double* re, double* im, double* amp);
+
 /* Observables of a state in caller-owned device memory, allocating nothing (the
  * paper has no counterpart; this serves callers that cannot allocate device memory
  * when they need the numbers: code running while a stream is captured into a CUDA

@@ -338,6 +338,102 @@ class Server:
         self.close()
 
 
+class LBParams(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32), ("Lx", ctypes.c_uint32), ("Ly", ctypes.c_uint32),
+        ("mode_mx", ctypes.c_int32), ("mode_my", ctypes.c_int32), ("init_weighted", ctypes.c_int32),
+        ("n0", ctypes.c_double), ("amp", ctypes.c_double), ("omega_j", ctypes.c_double),
+        ("omega", ctypes.c_double), ("theta", ctypes.c_double),
+    ]
+
+
+_lib.ilg_lb_create.argtypes = [ctypes.POINTER(LBParams), _vp, ctypes.POINTER(_vp)]
+_lib.ilg_lb_destroy.argtypes = [_vp]
+_lib.ilg_lb_last_error.argtypes = [_vp]
+_lib.ilg_lb_last_error.restype = ctypes.c_char_p
+_lib.ilg_lb_init.argtypes = [_vp]
+_lib.ilg_lb_set_state.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_uint64]
+_lib.ilg_lb_get_state.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
+_lib.ilg_lb_step.argtypes = [_vp, ctypes.c_uint32]
+_lib.ilg_lb_observables.argtypes = [_vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                    ctypes.POINTER(ctypes.c_double), _vp, _vp, _vp]
+for _f in ("ilg_lb_create", "ilg_lb_destroy", "ilg_lb_init", "ilg_lb_set_state", "ilg_lb_get_state", "ilg_lb_step",
+           "ilg_lb_observables"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+def lb_rates(omega_eff: float):
+    """(omega_j, omega) of the lattice gas with parameter omega_eff (the flip above 1)."""
+    return (omega_eff, 2.0 - omega_eff) if omega_eff > 1.0 else (omega_eff, omega_eff)
+
+
+class LB:
+    """Lattice Boltzmann comparator (ilg_lb_*), double precision on the device."""
+
+    def __init__(self, lattice, Lx, Ly=1, n0=10.0, amp=0.0, mode_mx=0, mode_my=0, init_weighted=0,
+                 omega_j=1.0, omega=1.0, theta=1.0 / 3.0, stream=None, **_ignored):
+        self.params = LBParams(int(lattice), int(Lx), int(Ly if lattice == D2Q5 else 1), int(mode_mx), int(mode_my),
+                               int(init_weighted), float(n0), float(amp), float(omega_j), float(omega), float(theta))
+        self.Q = 3 if lattice == D1Q3 else 5
+        self.Lx, self.Ly = self.params.Lx, self.params.Ly
+        h = _vp()
+        st = _lib.ilg_lb_create(ctypes.byref(self.params), _vp(stream_handle(stream)), ctypes.byref(h))
+        if st != ILG_OK:
+            raise IlgError(st, _lib.ilg_lb_last_error(None).decode(errors="replace"))
+        self._h = h
+
+    @property
+    def shape(self):
+        return (self.Q, self.Ly, self.Lx)
+
+    def _check(self, st):
+        if st != ILG_OK:
+            raise IlgError(st, _lib.ilg_lb_last_error(self._h).decode(errors="replace"))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ilg_lb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init(self):
+        self._check(_lib.ilg_lb_init(self._h))
+
+    def set_state(self, f: np.ndarray, t: int = 0):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        self._check(_lib.ilg_lb_set_state(self._h, f.ctypes.data, f.size, int(t)))
+
+    def get_state(self):
+        out = np.empty(self.shape, dtype=np.float64)
+        t = ctypes.c_uint64()
+        self._check(_lib.ilg_lb_get_state(self._h, out.ctypes.data, out.size, ctypes.byref(t)))
+        return out, int(t.value)
+
+    def step(self, T: int):
+        self._check(_lib.ilg_lb_step(self._h, int(T)))
+
+    def observables(self, modes=()):
+        modes = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, 2))
+        n = len(modes)
+        re, im, amp = (np.zeros(n) for _ in range(3))
+        t = ctypes.c_uint64()
+        M = ctypes.c_double()
+        self._check(_lib.ilg_lb_observables(self._h, modes.ctypes.data if n else None, n, ctypes.byref(t),
+                                            ctypes.byref(M), re.ctypes.data, im.ctypes.data, amp.ctypes.data))
+        return dict(t=int(t.value), mass=float(M.value), re=re, im=im, amp=amp)
+
+
 def observables_noalloc(lattice: int, Lx: int, Ly: int, state_dev_ptr: int, modes=(), stream=None):
     """ilg_observables_noalloc on a device state (see include/ilg.h)."""
     modes = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, 2))

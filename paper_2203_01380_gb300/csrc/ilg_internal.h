@@ -45,6 +45,10 @@ struct InitTables {
   std::vector<uint32_t> table;      // concatenated CDF entries
 };
 bool build_init_tables(const ilg_params& p, int Q, InitTables* out, std::string* err);
+// Initial Poisson mean of velocity class cls (0 rest, 1 moving; only 0 when the
+// means are not weighted) at phase residue r of period L, and that period.
+double initial_mean(const ilg_params& p, int Q, int cls, uint32_t r, uint32_t L);
+uint32_t initial_period(const ilg_params& p);
 
 void set_context_free_error(const std::string& msg);
 std::string validate_params(const ilg_params& p);   // empty when valid

@@ -134,7 +134,7 @@ static double profile_sine(uint32_t r, uint32_t L) {
 
 // Initial mean of velocity class c (0 = rest, 1 = moving; only class 0 when the
 // means are not weighted) at phase residue r.
-static double initial_mean(const ilg_params& p, int Q, int cls, uint32_t r, uint32_t L) {
+double initial_mean(const ilg_params& p, int Q, int cls, uint32_t r, uint32_t L) {
   const double s = (p.amp != 0.0 && L != 0) ? profile_sine(r, L) : 0.0;
   if (p.init_weighted) {
     double w[5];
@@ -145,10 +145,14 @@ static double initial_mean(const ilg_params& p, int Q, int cls, uint32_t r, uint
   return p.n0 + (p.amp * s) / static_cast<double>(Q);
 }
 
+uint32_t initial_period(const ilg_params& p) {
+  if (p.amp != 0.0 && p.mode_mx != 0) return p.Lx;
+  if (p.amp != 0.0 && p.mode_my != 0) return (p.lattice == ILG_D1Q3) ? 1 : p.Ly;
+  return 1;
+}
+
 bool build_init_tables(const ilg_params& p, int Q, InitTables* out, std::string* err) {
-  uint32_t L = 1;  // period of the phase residue
-  if (p.amp != 0.0 && p.mode_mx != 0) L = p.Lx;
-  else if (p.amp != 0.0 && p.mode_my != 0) L = (p.lattice == ILG_D1Q3) ? 1 : p.Ly;
+  const uint32_t L = initial_period(p);  // period of the phase residue
   const int classes = p.init_weighted ? 2 : 1;
   out->period = L;
   out->classes = classes;

@@ -70,3 +70,24 @@ def test_binding_refuses_to_import_without_library(tmp_path):
     r = subprocess.run(["python", "-c", "import sys; sys.path.insert(0, %r); import binding" % str(pkg)],
                        capture_output=True, text=True)
     assert r.returncode != 0 and "no CPU fallback" in r.stderr
+
+
+def test_lb_params_layout_matches_c(binding):
+    src = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "ilg.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(ilg_lb_params), offsetof(ilg_lb_params, n0),
+         offsetof(ilg_lb_params, omega_j), offsetof(ilg_lb_params, omega), offsetof(ilg_lb_params, theta));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    P = binding.LBParams
+    assert got == [ctypes.sizeof(P), P.n0.offset, P.omega_j.offset, P.omega.offset, P.theta.offset]
