@@ -15,6 +15,7 @@ oracle on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -60,6 +61,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self._summary = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -84,6 +86,11 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self._summary is None:
+            self._summary = self._read()
+        return self._summary
+
+    def _read(self):
         try:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
             os.unlink(self.path)
@@ -228,6 +235,39 @@ def measure_lb(torch, B, dev, clocks):
                          "peak_source": "nominal 1.25 TFLOP/s fp64 (2 FMA lanes per SM per cycle) at the measured SM clock"},
             "hbm": {"achieved": gbs, "peak": hpk, "unit": "GB/s", "frac": gbs / hpk},
             "mass": mass}
+
+
+def measure_ensemble(torch, B, dev):
+    """512 replicas of the L = 320 ring (Sec. V, Fig. 1) for 2000 steps with the
+    on-device ensemble statistics of mode 1; the decay of the replica-mean
+    amplitude fitted to exp(-D k^2 t) against D = theta (1/omega^j - 1/2)."""
+    cfg = dict(inputs.ENSEMBLE_D1Q3)
+    R, T = cfg.pop("replicas"), cfg.pop("steps")
+    reps = [dict(cfg, replica=r) for r in range(R)]
+    st = torch.cuda.Stream(dev)
+    with B.Batch(reps, stream=st) as bat:
+        bat.init()
+        bat.ensemble(10)
+        bat.init()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        stats = bat.ensemble(T, mode=1)
+        wall = time.perf_counter() - t0
+    L = cfg["Lx"]
+    amp = stats["mean_im"] / (L / 2.0)
+    ts = np.arange(T + 1)
+    sel = ts >= 200
+    slope = np.polyfit(ts[sel], np.log(amp[sel]), 1)[0]
+    k2 = (2 * np.pi / L) ** 2
+    oj = cfg["omega_eff"]
+    D_theory = cfg["theta"] * (1.0 / oj - 0.5)
+    return {"workload": f"ensemble_d1q3: {R} replicas of a D1Q3 ring L={L}, n0 {cfg['n0']:.2f}, sine amplitude "
+                        f"{cfg['amp']}, omega_eff {oj}, {T} steps, statistics of mode 1 at every step",
+            "value": R * L * T / wall / 1e9, "unit": "GNUPS", "seconds": wall,
+            "amplitude": {"t0": float(amp[0]), "t_end": float(amp[-1]),
+                          "sd_of_mean_t_end": float(math.sqrt(stats["var_im"][-1] / R) / (L / 2.0))},
+            "diffusion": {"fitted": float(-slope / k2), "theory": D_theory, "fit": "ln <A(t)>, t in [200, 2000]"},
+            "structure_factor_t0_over_mass": float(stats["cov_re"][0] / (cfg["n0"] * 3 * L))}
 
 
 def serve_stream(B, reqs, slots, smallest_first):
@@ -430,6 +470,7 @@ def main():
                                       "tile": "48 x 48 with a halo of depth nodes"}
         extra["batched"] = measure_batched(torch, B, dev)
         extra["lattice_boltzmann"] = measure_lb(torch, B, dev, clk.summary())
+        extra["ensemble"] = measure_ensemble(torch, B, dev)
         extra["serving"] = measure_serving(B)
 
     cpu = None

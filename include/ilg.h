@@ -139,7 +139,7 @@ ilg_status ilg_observables(ilg_ctx* ctx, const int32_t* modes, uint32_t nmodes, 
  * ring and its alias tables in shared memory for all steps, and write it back.
  * Results equal, bit for bit, those of one context per ring (ilg_create ...), as
  * every random number is keyed by the ring's replica word.  All rings of a batch
- * share one seed; Lx <= 16384 each.  Host arrays only; calls synchronise.
+ * share one seed; Lx <= 10240 each.  Host arrays only; calls synchronise.
  *   ilg_batch_create   params: n D1Q3 parameter sets (replica i = params[i]); tables
  *                      and device memory for all rings (stream NULL: a private one)
  *   ilg_batch_init     Poisson initial state of every ring (as ilg_init), t := 0
@@ -150,6 +150,22 @@ ilg_status ilg_observables(ilg_ctx* ctx, const int32_t* modes, uint32_t nmodes, 
  *                      ring stopped at the step that would exceed 65535 (its state
  *                      and t are those before that step); the others completed
  *   ilg_batch_observables   per ring: mass[i] and A^LG of one mode amp[i]
+ *   ilg_batch_ensemble T steps for every ring (as ilg_batch_run) while the complex
+ *                      amplitude a_r(t) = re + i im of axis mode `mode` of every
+ *                      ring r is recorded at the start (t = 0) and after each step
+ *                      (re, im as ilg_observables: sum_x cos|sin(2 pi (mode x mod L)
+ *                      / L) (L N(x) - M) / L), then reduced over the rings on the
+ *                      device, per t = 0..T (stats: 6 (T+1) doubles, row k at
+ *                      [k (T+1) + t]):  k = 0, 1  ensemble means of re and im;
+ *                      k = 2, 3  sample variances of re and im (divisor n - 1);
+ *                      k = 4, 5  real and imaginary parts of the connected
+ *                      correlation sum_r (a_r(t) - <a(t)>) conj(a_r(0) - <a(0)>) / (n - 1).
+ *                      With Poisson starts these are the replica averages of Sec. V
+ *                      (<A^LG(t)> = mean im / (L/2)) and the dynamic structure
+ *                      factor S(k, t) = k=4 row / L.  record (may be NULL) receives
+ *                      the per-ring values, [(r (T+1) + t) 2 + {0: re, 1: im}].
+ *                      Needs n >= 2 rings of one length L and mode not a multiple of
+ *                      L (ILG_E_INVALID otherwise).  Sums in a fixed order.
  * --------------------------------------------------------------------------- */
 typedef struct ilg_batch ilg_batch;
 ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, ilg_batch** out);
@@ -160,6 +176,7 @@ ilg_status ilg_batch_set_state(ilg_batch* b, uint32_t i, const uint16_t* host, s
 ilg_status ilg_batch_get_state(ilg_batch* b, uint32_t i, uint16_t* host, size_t n, uint64_t* t);
 ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record);
 ilg_status ilg_batch_observables(ilg_batch* b, int32_t mode, uint64_t* mass, double* amp);
+ilg_status ilg_batch_ensemble(ilg_batch* b, uint32_t T, int32_t mode, double* stats, double* record);
 
 /* ---------------------------------------------------------------------------
  * Serving loop for D2Q5 lattice requests (continuous batching).  A worker thread

@@ -149,3 +149,38 @@ class LB:
             re_s, im_s = math.fsum(re), math.fsum(im)
             out.append((re_s, im_s, im_s / (self.Lx * self.Ly / 2.0)))
         return M, out
+
+
+def ensemble_prediction(lb: LB, f0: np.ndarray, mode: int, T: int) -> dict:
+    """Exact ensemble statistics of the lattice gas's mode amplitude a(t) = re + i im,
+    re = sum_x cos(2 pi r / L) N(x), im = sum_x sin(2 pi r / L) N(x) (r = (mode x) mod L,
+    D1Q3 ring, mode not a multiple of L), for replicas started from independent
+    Poisson occupations with means f0, at t = 0..T.
+
+    Binomial thinning, multinomial redistribution, the flip and streaming map
+    independent Poisson occupations to independent Poisson occupations, and the
+    conditional mean of one step is the lattice Boltzmann step (Sec. IV).  So at
+    every t the occupations are independent Poisson with means f(t) = LB^t f0, and
+    Cov(n(t), n(0)) = LB^t diag(f0).  Hence
+      <re>, <im>     = projections of rho(t) = sum_i f_i(t)
+      Var re, Var im = sum_x cos^2 rho(t), sum_x sin^2 rho(t)
+      <da(t) conj(da(0))> = sum_x e(x) [rho_c(x, t) - i rho_s(x, t)],
+    with e = cos + i sin and rho_c, rho_s the densities of LB^t (f0 cos), LB^t (f0 sin)."""
+    L = lb.Lx
+    x = np.arange(L)
+    r = (mode * x) % L
+    c = np.array([math.cos(2.0 * math.pi * v / L) for v in r])
+    s = np.array([math.sin(2.0 * math.pi * v / L) for v in r])
+    f, fc, fs = f0.copy(), f0 * c[None, None, :], f0 * s[None, None, :]
+    out = {k: np.zeros(T + 1) for k in ("mean_re", "mean_im", "var_re", "var_im", "cov_re", "cov_im")}
+    for t in range(T + 1):
+        rho, rc, rs = f.sum(axis=0)[0], fc.sum(axis=0)[0], fs.sum(axis=0)[0]
+        out["mean_re"][t] = math.fsum(c * rho)
+        out["mean_im"][t] = math.fsum(s * rho)
+        out["var_re"][t] = math.fsum(c * c * rho)
+        out["var_im"][t] = math.fsum(s * s * rho)
+        out["cov_re"][t] = math.fsum(np.concatenate([c * rc, s * rs]))
+        out["cov_im"][t] = math.fsum(np.concatenate([s * rc, -c * rs]))
+        if t < T:
+            f, fc, fs = lb.step(f), lb.step(fc), lb.step(fs)
+    return out

@@ -74,6 +74,7 @@ _lib.ilg_batch_set_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t,
 _lib.ilg_batch_get_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
 _lib.ilg_batch_run.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp]
 _lib.ilg_batch_observables.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
+_lib.ilg_batch_ensemble.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp, _vp]
 class Result(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_uint32),
                 ("t", ctypes.c_uint64), ("mass", ctypes.c_uint64), ("amp", ctypes.c_double), ("Sk", ctypes.c_double),
@@ -99,6 +100,7 @@ for _f in ("ilg_set_temporal_blocking", "ilg_create", "ilg_destroy", "ilg_init",
            "ilg_get_state_device", "ilg_step", "ilg_observables", "ilg_philox", "ilg_binomial_table",
            "ilg_alias_table", "ilg_poisson_table", "ilg_observables_noalloc", "ilg_batch_create", "ilg_batch_destroy",
            "ilg_batch_init", "ilg_batch_set_state", "ilg_batch_get_state", "ilg_batch_run", "ilg_batch_observables",
+           "ilg_batch_ensemble",
            "ilg_server_create", "ilg_server_submit", "ilg_server_poll", "ilg_server_wait_idle", "ilg_server_stats",
            "ilg_server_destroy", "ilg_server_set_policy"):
     getattr(_lib, _f).restype = ctypes.c_int
@@ -271,6 +273,21 @@ class Batch:
         amp = np.zeros(self.n)
         self._check(_lib.ilg_batch_observables(self._h, int(mode), mass.ctypes.data, amp.ctypes.data))
         return mass, amp
+
+    ENSEMBLE_ROWS = ("mean_re", "mean_im", "var_re", "var_im", "cov_re", "cov_im")
+
+    def ensemble(self, T, mode=1, record=False):
+        """T steps with the ensemble statistics of mode `mode` at t = 0..T (dict of
+        arrays named as ENSEMBLE_ROWS) and, optionally, the per-ring record
+        (n, T + 1, 2) of (re, im)."""
+        stats = np.zeros((6, T + 1))
+        rec = np.zeros((self.n, T + 1, 2)) if record else None
+        self._check(_lib.ilg_batch_ensemble(self._h, int(T), int(mode), stats.ctypes.data,
+                                            rec.ctypes.data if rec is not None else None))
+        out = dict(zip(self.ENSEMBLE_ROWS, stats))
+        if record:
+            out["record"] = rec
+        return out
 
 
 class Server:

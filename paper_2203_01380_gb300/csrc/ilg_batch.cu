@@ -51,8 +51,99 @@ __device__ double block_dot2(double s, double c, double* red) {
   return r;  // valid in thread 0
 }
 
+// Exact 128-bit integer accumulator of products of int64 values.
+struct I128 {
+  unsigned long long lo = 0;
+  long long hi = 0;
+  __device__ __forceinline__ void add(unsigned long long l, long long h) {
+    const unsigned long long n = lo + l;
+    hi += h + (n < lo ? 1 : 0);
+    lo = n;
+  }
+  __device__ __forceinline__ void add_product(long long a, long long b) {
+    add((unsigned long long)(a * b), __mul64hi(a, b));
+  }
+};
+
+// v * 2^-62 rounded once to double (round to nearest even).
+__device__ double i128_to_double_2m62(I128 v) {
+  const bool neg = v.hi < 0;
+  unsigned long long lo = v.lo, hi = (unsigned long long)v.hi;
+  if (neg) {  // two's complement negation
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0 ? 1ull : 0ull);
+  }
+  double mag;
+  if (hi == 0) {
+    mag = __ull2double_rn(lo);
+  } else {
+    // keep the top 64 bits, fold the rest into a sticky bit: one correct rounding
+    const int k = 64 - __clzll((long long)hi);  // significant bits of hi, 1..64
+    unsigned long long m = k == 64 ? hi : ((hi << (64 - k)) | (lo >> k));
+    const unsigned long long dropped = k == 64 ? lo : (lo << (64 - k));
+    if (dropped) m |= 1ull;
+    mag = ldexp(__ull2double_rn(m), k);
+  }
+  const double r = ldexp(mag, -62);
+  return neg ? -r : r;
+}
+
+// Fixed-point (2^-62) cosine and sine of 2 pi r / L.
+__device__ __forceinline__ longlong2 trig_fixed(uint32_t r, uint32_t L) {
+  double sn, cs;
+  sincospi(2.0 * double(r) / double(L), &sn, &cs);
+  return make_longlong2(__double2ll_rn(ldexp(cs, 62)), __double2ll_rn(ldexp(sn, 62)));
+}
+
+// Complex amplitude of axis mode m of a ring held in shared memory (buf, planes
+// Lmax apart): with D(x) = L N(x) - M and r = (m x) mod L,
+//   re = sum_x cos(2 pi r / L) D(x) / L,  im = sum_x sin(2 pi r / L) D(x) / L.
+// The trigonometric values enter as 2^-62 fixed-point integers (from trig, indexed
+// by x, when given) and the sums are exact in 128-bit integers, so the result is
+// independent of the summation order and rounded once.  Valid in thread 0; every
+// thread must call it.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, StepArgs common) {
+__device__ void ring_projection(const uint16_t* buf, uint32_t L, uint32_t Lmax, uint64_t mass, uint32_t m,
+                                const longlong2* trig, unsigned long long* red, double& re, double& im) {
+  I128 ac, as;
+  for (uint32_t x = threadIdx.x; x < L; x += THREADS) {
+    const long long N = (long long)buf[x] + buf[Lmax + x] + buf[2 * Lmax + x];
+    const long long D = (long long)L * N - (long long)mass;
+    const longlong2 cs = trig ? trig[x] : trig_fixed(uint32_t((uint64_t(m) * x) % L), L);
+    ac.add_product(cs.x, D);
+    as.add_product(cs.y, D);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long cl = __shfl_down_sync(0xFFFFFFFFu, ac.lo, o);
+    const long long ch = __shfl_down_sync(0xFFFFFFFFu, ac.hi, o);
+    const unsigned long long sl = __shfl_down_sync(0xFFFFFFFFu, as.lo, o);
+    const long long sh = __shfl_down_sync(0xFFFFFFFFu, as.hi, o);
+    ac.add(cl, ch);
+    as.add(sl, sh);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[4 * warp + 0] = ac.lo;
+    red[4 * warp + 1] = (unsigned long long)ac.hi;
+    red[4 * warp + 2] = as.lo;
+    red[4 * warp + 3] = (unsigned long long)as.hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    I128 c, s;
+    for (int w = 0; w < THREADS / 32; ++w) {
+      c.add(red[4 * w + 0], (long long)red[4 * w + 1]);
+      s.add(red[4 * w + 2], (long long)red[4 * w + 3]);
+    }
+    re = i128_to_double_2m62(c) / double(L);
+    im = i128_to_double_2m62(s) / double(L);
+  }
+  __syncthreads();
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(BatchArgs b, StepArgs common) {
   extern __shared__ uint4 smem4[];
   uint32_t* tables = reinterpret_cast<uint32_t*>(smem4);                     // kDevBlockWords words
   uint32_t* xbuf = tables + kDevBlockWords;                                   // kBatchExtWords x THREADS
@@ -60,7 +151,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, Ste
   __shared__ uint32_t s_task;
   __shared__ int s_fail;
   __shared__ unsigned long long s_mass;
-  __shared__ double s_red[2 * (THREADS / 32)];
+  __shared__ unsigned long long s_red[4 * (THREADS / 32)];
   const int tid = threadIdx.x;
 
   for (;;) {
@@ -104,6 +195,13 @@ __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, Ste
       if (part) atomicAdd(&s_mass, part);
       __syncthreads();
       mass = s_mass;
+      double re, im;
+      ring_projection<THREADS>(buf0, L, b.Lmax, mass, mrec, b.trig, s_red, re, im);
+      if (tid == 0) {
+        double* o = b.record + size_t(r) * (b.T + 1) * 2;
+        o[0] = re;
+        o[1] = im;
+      }
     }
 
     uint16_t* src = buf0;
@@ -136,23 +234,14 @@ __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, Ste
       dst = tmp;
       steps_done = s + 1;
       if (rec) {
-        // amplitude projection of the new state (t + 1): sum_x s(x) (L N(x) - M) / L
-        double ps = 0.0, pc = 0.0;
-        for (uint32_t x = tid; x < L; x += THREADS) {
-          const long long N = (long long)src[x] + src[b.Lmax + x] + src[2 * b.Lmax + x];
-          const long long D = (long long)L * N - (long long)mass;
-          const uint32_t rr = uint32_t((uint64_t(mrec) * x) % L);
-          double sn, cs;
-          sincospi(2.0 * double(rr) / double(L), &sn, &cs);
-          const double p = sn * double(D);
-          const double pe = fma(sn, double(D), -p);
-          double q;
-          two_sum_b(ps, p, ps, q);
-          pc += q + pe;
+        // complex amplitude of the new state (t + 1)
+        double re, im;
+        ring_projection<THREADS>(src, L, b.Lmax, mass, mrec, b.trig, s_red, re, im);
+        if (tid == 0) {
+          double* o = b.record + (size_t(r) * (b.T + 1) + s + 1) * 2;
+          o[0] = re;
+          o[1] = im;
         }
-        const double im = block_dot2<THREADS>(ps, pc, s_red) / double(L);
-        if (tid == 0) b.record[size_t(r) * b.T + s] = im / (double(L) / 2.0);
-        __syncthreads();
       }
     }
     // ring back to global memory; the replica's step counter moves on
@@ -168,20 +257,34 @@ __global__ void __launch_bounds__(THREADS, 1) batch_d1q3_kernel(BatchArgs b, Ste
 
 }  // namespace
 
+// Rings up to kBatchSmallL nodes run on 256-thread blocks, four per SM; longer
+// rings on one 1024-thread block per SM.
 constexpr int kBatchThreads = 1024;
+constexpr int kBatchSmallThreads = 256;
+constexpr uint32_t kBatchSmallL = 1024;
 
-size_t batch_smem_bytes(uint32_t Lmax) {
-  return sizeof(uint32_t) * (kDevBlockWords + size_t(kBatchExtWords) * kBatchThreads) +
+size_t batch_smem_bytes(uint32_t Lmax, int threads) {
+  return sizeof(uint32_t) * (kDevBlockWords + size_t(kBatchExtWords) * threads) +
          sizeof(uint16_t) * 2 * 3 * size_t(Lmax);
 }
 
 cudaError_t prepare_batch_kernel(uint32_t Lmax) {
+  if (Lmax <= kBatchSmallL)
+    return cudaFuncSetAttribute(batch_d1q3_kernel<kBatchSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(batch_smem_bytes(Lmax, kBatchSmallThreads)));
   return cudaFuncSetAttribute(batch_d1q3_kernel<kBatchThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(batch_smem_bytes(Lmax)));
+                              int(batch_smem_bytes(Lmax, kBatchThreads)));
 }
 
-cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int grid, cudaStream_t s) {
-  batch_d1q3_kernel<kBatchThreads><<<grid, kBatchThreads, batch_smem_bytes(b.Lmax), s>>>(b, common);
+cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int sms, cudaStream_t s) {
+  if (b.Lmax <= kBatchSmallL) {
+    const int grid = int(b.n < uint32_t(4 * sms) ? b.n : uint32_t(4 * sms));
+    batch_d1q3_kernel<kBatchSmallThreads>
+        <<<grid, kBatchSmallThreads, batch_smem_bytes(b.Lmax, kBatchSmallThreads), s>>>(b, common);
+  } else {
+    const int grid = int(b.n < uint32_t(sms) ? b.n : uint32_t(sms));
+    batch_d1q3_kernel<kBatchThreads><<<grid, kBatchThreads, batch_smem_bytes(b.Lmax, kBatchThreads), s>>>(b, common);
+  }
   return cudaGetLastError();
 }
 
@@ -228,11 +331,99 @@ __global__ void __launch_bounds__(256) batch_obs_kernel(const ReplicaDesc* __res
   }
 }
 
+// trig[x] = fixed-point (cos, sin) of 2 pi ((m x) mod L) / L, x = 0..L-1.
+__global__ void batch_trig_kernel(uint32_t L, uint32_t m, longlong2* __restrict__ trig) {
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < L; x += gridDim.x * blockDim.x)
+    trig[x] = trig_fixed(uint32_t((uint64_t(m) * x) % L), L);
+}
+
+// amp[r T + s] = im / (L_r / 2) of the record entry after step s.
+__global__ void batch_amp_kernel(const ReplicaDesc* __restrict__ desc, const double* __restrict__ record,
+                                 uint32_t n, uint32_t T, double* __restrict__ amp) {
+  const size_t total = size_t(n) * T;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+    const size_t r = i / T, s = i - r * T;
+    amp[i] = record[(r * (T + 1) + s + 1) * 2 + 1] / (double(desc[r].L) / 2.0);
+  }
+}
+
+// Ensemble statistics over the n rings of the record, one block per time index t:
+// means of re and im, sample variances (divisor n - 1) and the connected
+// correlation with t = 0 of a = re + i im:  cov = sum (a(t) - <a(t)>) conj(a(0) - <a(0)>) / (n - 1).
+// Fixed-order sums (deterministic); two passes (means, then deviations).
+__global__ void __launch_bounds__(256) batch_ensemble_kernel(const double* __restrict__ record, uint32_t n,
+                                                             uint32_t T, double* __restrict__ out) {
+  __shared__ double red[4][256];
+  const uint32_t t = blockIdx.x;
+  const size_t stride = size_t(T + 1) * 2;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double* o = record + r * stride;
+    v[0] += o[2 * t];
+    v[1] += o[2 * t + 1];
+    v[2] += o[0];
+    v[3] += o[1];
+  }
+  auto reduce4 = [&](double (&w)[4]) {
+    for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = w[k];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+      if (int(threadIdx.x) < h)
+        for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
+      __syncthreads();
+    }
+    for (int k = 0; k < 4; ++k) w[k] = red[k][0];
+    __syncthreads();
+  };
+  reduce4(v);
+  const double mre = v[0] / n, mim = v[1] / n, m0re = v[2] / n, m0im = v[3] / n;
+  double w[4] = {0.0, 0.0, 0.0, 0.0};
+  for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double* o = record + r * stride;
+    const double dre = o[2 * t] - mre, dim = o[2 * t + 1] - mim;
+    const double d0re = o[0] - m0re, d0im = o[1] - m0im;
+    w[0] += dre * dre;
+    w[1] += dim * dim;
+    w[2] += dre * d0re + dim * d0im;
+    w[3] += dim * d0re - dre * d0im;
+  }
+  reduce4(w);
+  if (threadIdx.x == 0) {
+    const size_t P = T + 1;
+    const double dn = double(n) - 1.0;
+    out[0 * P + t] = mre;
+    out[1 * P + t] = mim;
+    out[2 * P + t] = w[0] / dn;
+    out[3 * P + t] = w[1] / dn;
+    out[4 * P + t] = w[2] / dn;
+    out[5 * P + t] = w[3] / dn;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_batch_obs(const ReplicaDesc* desc, const uint16_t* state, uint32_t n, int32_t mode,
                              unsigned long long* mass, double* amp, cudaStream_t s) {
   batch_obs_kernel<<<n, 256, 0, s>>>(desc, state, mode, mass, amp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_amp(const ReplicaDesc* desc, const double* record, uint32_t n, uint32_t T, double* amp,
+                             cudaStream_t s) {
+  const size_t total = size_t(n) * T;
+  const int grid = int(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096);
+  batch_amp_kernel<<<grid, 256, 0, s>>>(desc, record, n, T, amp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_trig(uint32_t L, int32_t mode, longlong2* trig, cudaStream_t s) {
+  const uint32_t m = uint32_t(((int64_t(mode) % int64_t(L)) + L) % L);
+  batch_trig_kernel<<<(L + 255) / 256, 256, 0, s>>>(L, m, trig);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ensemble(const double* record, uint32_t n, uint32_t T, double* out, cudaStream_t s) {
+  batch_ensemble_kernel<<<T + 1, 256, 0, s>>>(record, n, T, out);
   return cudaGetLastError();
 }
 

@@ -36,13 +36,20 @@ struct BatchArgs {
   uint16_t* state;
   unsigned int* counter;   // work queue head, 0 at launch
   uint32_t* failed;        // per replica: 1 when a step would exceed 65535
-  double* record;          // n x T amplitudes A^LG after every step, or NULL
+  double* record;          // n x (T + 1) x (re, im) of the recorded mode: at the launch's
+                           // start, then after every step; or NULL
+  const longlong2* trig;   // fixed-point (cos, sin) of the recorded mode indexed by x when
+                           // every ring has one length, else NULL (computed per node)
 };
 
-size_t batch_smem_bytes(uint32_t Lmax);
+size_t batch_smem_bytes(uint32_t Lmax, int threads);
 cudaError_t prepare_batch_kernel(uint32_t Lmax);
-cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int grid, cudaStream_t s);
+cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int sms, cudaStream_t s);
 cudaError_t launch_batch_obs(const ReplicaDesc* desc, const uint16_t* state, uint32_t n, int32_t mode,
                              unsigned long long* mass, double* amp, cudaStream_t s);
+cudaError_t launch_batch_amp(const ReplicaDesc* desc, const double* record, uint32_t n, uint32_t T, double* amp,
+                             cudaStream_t s);
+cudaError_t launch_batch_trig(uint32_t L, int32_t mode, longlong2* trig, cudaStream_t s);
+cudaError_t launch_batch_ensemble(const double* record, uint32_t n, uint32_t T, double* out, cudaStream_t s);
 
 }  // namespace ilg

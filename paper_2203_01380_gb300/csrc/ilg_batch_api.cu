@@ -33,12 +33,17 @@ struct ilg_batch {
   uint32_t* d_failed = nullptr;
   double* d_record = nullptr;
   size_t record_cap = 0;
+  double* d_out = nullptr;            // amplitude record or ensemble statistics
+  size_t out_cap = 0;
+  longlong2* d_trig = nullptr;        // fixed-point trigonometric table of the ensemble mode
+  uint32_t trig_cap = 0;
   unsigned long long* d_mass = nullptr;
   double* d_amp = nullptr;
   StepArgs common{};
   cudaGraphExec_t graph = nullptr;
   uint32_t graph_T = 0;
   bool graph_rec = false;
+  bool graph_trig = false;
   int32_t graph_mode = 0;
   std::string err;
 };
@@ -79,6 +84,8 @@ void free_batch(ilg_batch* b) {
   cudaFree(b->d_counter);
   cudaFree(b->d_failed);
   cudaFree(b->d_record);
+  cudaFree(b->d_out);
+  cudaFree(b->d_trig);
   cudaFree(b->d_mass);
   cudaFree(b->d_amp);
   if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -250,24 +257,45 @@ ilg_status ilg_batch_get_state(ilg_batch* b, uint32_t i, uint16_t* host, size_t 
   return ILG_OK;
 }
 
-ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record) {
-  if (!b) return ILG_E_INVALID;
-  if (T == 0) return ILG_OK;
+namespace {
+
+// Queue one persistent launch of T steps (graph-captured, re-captured when T, the
+// record flag or the mode change) and the read-back of the per-ring flags and
+// descriptors.  With rec the complex amplitude of record_mode is recorded at the
+// start and after every step (n x (T + 1) x 2 doubles in d_record).
+ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec, bool trig,
+                        std::vector<uint32_t>& failed) {
   for (const auto& d : b->desc)
     if (uint64_t(d.t) + T >= (uint64_t(1) << 32)) return bfail(b, ILG_E_INVALID, "step counter would reach 2^32");
-  const bool rec = amp_record != nullptr;
-  if (rec && b->record_cap < size_t(b->n) * T) {
+  const size_t need = size_t(b->n) * (size_t(T) + 1) * 2;
+  if (rec && b->record_cap < need) {
     cudaFree(b->d_record);
     b->d_record = nullptr;
     b->record_cap = 0;
-    BCUDA(b, cudaMalloc(&b->d_record, sizeof(double) * b->n * size_t(T)), "cudaMalloc record");
-    b->record_cap = size_t(b->n) * T;
+    BCUDA(b, cudaMalloc(&b->d_record, sizeof(double) * need), "cudaMalloc record");
+    b->record_cap = need;
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
     }
   }
-  if (!b->graph || b->graph_T != T || b->graph_rec != rec || b->graph_mode != record_mode) {
+  if (trig) {
+    // every ring has length desc[0].L: one table indexed by x, rebuilt each call
+    const uint32_t L = b->desc[0].L;
+    if (b->trig_cap < L) {
+      cudaFree(b->d_trig);
+      b->d_trig = nullptr;
+      b->trig_cap = 0;
+      BCUDA(b, cudaMalloc(&b->d_trig, sizeof(longlong2) * L), "cudaMalloc trig");
+      b->trig_cap = L;
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+    }
+    BCUDA(b, launch_batch_trig(L, record_mode, b->d_trig, b->stream), "trig table");
+  }
+  if (!b->graph || b->graph_T != T || b->graph_rec != rec || b->graph_mode != record_mode || b->graph_trig != trig) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     BatchArgs a{};
@@ -282,12 +310,12 @@ ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* 
     a.counter = b->d_counter;
     a.failed = b->d_failed;
     a.record = rec ? b->d_record : nullptr;
-    const int grid = int(std::min<uint32_t>(b->n, uint32_t(b->sms)));
+    a.trig = trig ? b->d_trig : nullptr;
     cudaGraph_t g = nullptr;
     BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_failed, 0, sizeof(uint32_t) * b->n, b->stream);
-    if (e == cudaSuccess) e = launch_batch(a, b->common, grid, b->stream);
+    if (e == cudaSuccess) e = launch_batch(a, b->common, b->sms, b->stream);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -299,14 +327,17 @@ ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* 
     b->graph_T = T;
     b->graph_rec = rec;
     b->graph_mode = record_mode;
+    b->graph_trig = trig;
   }
   BCUDA(b, cudaGraphLaunch(b->graph, b->stream), "batch launch");
-  std::vector<uint32_t> failed(b->n);
+  failed.assign(b->n, 0);
   BCUDA(b, cudaMemcpyAsync(failed.data(), b->d_failed, sizeof(uint32_t) * b->n, cudaMemcpyDeviceToHost, b->stream), "read flags");
   BCUDA(b, cudaMemcpyAsync(b->desc.data(), b->d_desc, sizeof(ReplicaDesc) * b->n, cudaMemcpyDeviceToHost, b->stream), "read desc");
-  if (rec)
-    BCUDA(b, cudaMemcpyAsync(amp_record, b->d_record, sizeof(double) * b->n * size_t(T), cudaMemcpyDeviceToHost, b->stream),
-          "read record");
+  return ILG_OK;
+}
+
+// Wait for the queued work; ILG_E_OVERFLOW if a ring stopped.
+ilg_status batch_finish(ilg_batch* b, const std::vector<uint32_t>& failed) {
   BCUDA(b, cudaStreamSynchronize(b->stream), "batch run");
   uint32_t nf = 0, first = 0;
   for (uint32_t i = 0; i < b->n; ++i)
@@ -321,6 +352,59 @@ ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* 
     return bfail(b, ILG_E_OVERFLOW, buf);
   }
   return ILG_OK;
+}
+
+ilg_status ensure_doubles(ilg_batch* b, double** buf, size_t* cap, size_t need) {
+  if (*cap >= need) return ILG_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  BCUDA(b, cudaMalloc(buf, sizeof(double) * need), "cudaMalloc");
+  *cap = need;
+  return ILG_OK;
+}
+
+}  // namespace
+
+ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record) {
+  if (!b) return ILG_E_INVALID;
+  if (T == 0) return ILG_OK;
+  const bool rec = amp_record != nullptr;
+  std::vector<uint32_t> failed;
+  if (rec) {
+    const ilg_status st = ensure_doubles(b, &b->d_out, &b->out_cap, size_t(b->n) * T);
+    if (st != ILG_OK) return st;
+  }
+  ilg_status st = batch_launch(b, T, record_mode, rec, false, failed);
+  if (st != ILG_OK) return st;
+  if (rec) {
+    BCUDA(b, launch_batch_amp(b->d_desc, b->d_record, b->n, T, b->d_out, b->stream), "amplitude record");
+    BCUDA(b, cudaMemcpyAsync(amp_record, b->d_out, sizeof(double) * b->n * size_t(T), cudaMemcpyDeviceToHost, b->stream),
+          "read record");
+  }
+  return batch_finish(b, failed);
+}
+
+ilg_status ilg_batch_ensemble(ilg_batch* b, uint32_t T, int32_t mode, double* stats, double* record) {
+  if (!b) return ILG_E_INVALID;
+  if (!stats) return bfail(b, ILG_E_INVALID, "stats is NULL");
+  if (b->n < 2) return bfail(b, ILG_E_INVALID, "an ensemble needs at least two rings");
+  for (const auto& d : b->desc)
+    if (d.L != b->desc[0].L) return bfail(b, ILG_E_INVALID, "ensemble statistics need rings of one length");
+  if (mode % int64_t(b->desc[0].L) == 0) return bfail(b, ILG_E_INVALID, "the mode must not be a multiple of L");
+  ilg_status st = ensure_doubles(b, &b->d_out, &b->out_cap, 6 * (size_t(T) + 1));
+  if (st != ILG_OK) return st;
+  std::vector<uint32_t> failed;
+  st = batch_launch(b, T, mode, true, true, failed);
+  if (st != ILG_OK) return st;
+  BCUDA(b, launch_batch_ensemble(b->d_record, b->n, T, b->d_out, b->stream), "ensemble statistics");
+  BCUDA(b, cudaMemcpyAsync(stats, b->d_out, sizeof(double) * 6 * (size_t(T) + 1), cudaMemcpyDeviceToHost, b->stream),
+        "read statistics");
+  if (record)
+    BCUDA(b, cudaMemcpyAsync(record, b->d_record, sizeof(double) * 2 * b->n * (size_t(T) + 1), cudaMemcpyDeviceToHost,
+                             b->stream),
+          "read record");
+  return batch_finish(b, failed);
 }
 
 ilg_status ilg_batch_observables(ilg_batch* b, int32_t mode, uint64_t* mass, double* amp) {

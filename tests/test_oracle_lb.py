@@ -157,3 +157,46 @@ def test_lattice_gas_mean_is_lattice_boltzmann():
     chi2 = float((((mean - f) ** 2) / (f / R)).sum())
     # chi-square with 48 degrees of freedom: outside [14, 110] has probability < 1e-6
     assert 14 < chi2 < 110, chi2
+
+
+def test_ensemble_prediction_against_gas_replicas():
+    """The exact ensemble statistics (product-Poisson propagation through the lattice
+    Boltzmann map) against R replicas of the integer oracle: means, variances and the
+    connected correlation with t = 0 of the complex mode amplitude, each within six
+    standard errors."""
+    cfg = dict(n0=15.0, amp=12.0, mode_mx=1, init_weighted=1, omega_eff=1.7, seed=29)
+    Lr, T, R, mode = 12, 8, 2500, 1
+    oj, om = L.rates_from_omega_eff(cfg["omega_eff"])
+    lb = L.LB(O.D1Q3, Lr, omega_j=oj, omega=om)
+    f0 = lb.init_mean(n0=15.0, amp=12.0, mode_mx=1, init_weighted=1)
+    pred = L.ensemble_prediction(lb, f0, mode, T)
+    lat = O.Lattice(O.D1Q3, Lr, **cfg)
+    x = np.arange(Lr)
+    cs = np.cos(2 * np.pi * ((mode * x) % Lr) / Lr)
+    sn = np.sin(2 * np.pi * ((mode * x) % Lr) / Lr)
+    rec = np.zeros((R, T + 1), dtype=complex)
+    for r in range(R):
+        lat.replica = r
+        s = lat.init()
+        for t in range(T + 1):
+            N = s.sum(axis=0)[0].astype(float)
+            rec[r, t] = (cs * N).sum() + 1j * (sn * N).sum()
+            if t < T:
+                s = lat.step(s, t)
+    m = rec.mean(axis=0)
+    d = rec - m[None, :]
+    var_re = (d.real ** 2).sum(axis=0) / (R - 1)
+    var_im = (d.imag ** 2).sum(axis=0) / (R - 1)
+    cov = (d * np.conj(d[:, :1])).sum(axis=0) / (R - 1)
+    for t in range(T + 1):
+        assert abs(m[t].real - pred["mean_re"][t]) < 6 * math.sqrt(pred["var_re"][t] / R)
+        assert abs(m[t].imag - pred["mean_im"][t]) < 6 * math.sqrt(pred["var_im"][t] / R)
+        assert abs(var_re[t] / pred["var_re"][t] - 1) < 6 * math.sqrt(2 / R) + 0.02
+        assert abs(var_im[t] / pred["var_im"][t] - 1) < 6 * math.sqrt(2 / R) + 0.02
+        tot0 = pred["var_re"][0] + pred["var_im"][0]
+        tot = pred["var_re"][t] + pred["var_im"][t]
+        se = math.sqrt(tot * tot0 / R)
+        assert abs(cov[t].real - pred["cov_re"][t]) < 6 * se, t
+        assert abs(cov[t].imag - pred["cov_im"][t]) < 6 * se, t
+    # the correlation must actually decay (omega^j = 1.7: D > 0)
+    assert pred["cov_re"][T] < 0.97 * pred["cov_re"][0]
