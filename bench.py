@@ -203,9 +203,11 @@ LB_FP64_OPS_PER_NU = 15         # D2Q5: 4 adds, 2 multiplies, 9 fused multiply-a
 LB_BYTES_PER_NU = 80            # 5 doubles read + 5 written
 
 
-def measure_lb(torch, B, dev, clocks):
+def measure_lb(torch, B, dev, clocks, side=None):
     """Lattice Boltzmann comparator (Sec. IV) on the 16384^2 D2Q5 lattice, 100 steps."""
     cfg = dict(inputs.LB_D2Q5)
+    if side:
+        cfg.update(Lx=side, Ly=side)
     oj, om = B.lb_rates(cfg["omega_eff"])
     kw = {k: v for k, v in cfg.items() if k not in ("omega_eff", "steps")}
     st = torch.cuda.Stream(dev)
@@ -368,7 +370,10 @@ def main():
     ap.add_argument("--tsteps", type=int, default=inputs.LARGE_D2Q5["steps"], help="lattice steps per bench step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-modes", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--no-modes", action="store_true", help="skip every measurement beyond the main workload")
+    ap.add_argument("--extra", default="tb,batched,lb,ensemble,serving",
+                    help="comma-separated measurements beyond the main workload")
+    ap.add_argument("--lb-side", type=int, default=0, help="side of the lattice Boltzmann workload (default 16384)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     cfg = {k: v for k, v in inputs.LARGE_D2Q5.items() if k != "steps"}
@@ -455,7 +460,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_modes:
         # temporal blocking on the same workload: steps per launch against single steps
         tb = {}
-        for depth in (2, 4):
+        parts = set(args.extra.split(","))
+        for depth in ((2, 4) if "tb" in parts else ()):
             lat.set_temporal_blocking(depth)
             lat.step(2 * depth)
             ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -466,12 +472,17 @@ def main():
             torch.cuda.synchronize(dev)
             tb[str(depth)] = {"value": nodes * 100 / (ea.elapsed_time(eb) / 1e3) / 1e9, "unit": "GNUPS"}
         lat.set_temporal_blocking(0)
-        extra["temporal_blocking"] = {"steps_per_launch": tb, "single_step_kernel": {"value": value, "unit": "GNUPS"},
-                                      "tile": "48 x 48 with a halo of depth nodes"}
-        extra["batched"] = measure_batched(torch, B, dev)
-        extra["lattice_boltzmann"] = measure_lb(torch, B, dev, clk.summary())
-        extra["ensemble"] = measure_ensemble(torch, B, dev)
-        extra["serving"] = measure_serving(B)
+        if tb:
+            extra["temporal_blocking"] = {"steps_per_launch": tb, "single_step_kernel": {"value": value, "unit": "GNUPS"},
+                                          "tile": "48 x 48 with a halo of depth nodes"}
+        if "batched" in parts:
+            extra["batched"] = measure_batched(torch, B, dev)
+        if "lb" in parts:
+            extra["lattice_boltzmann"] = measure_lb(torch, B, dev, clk.summary(), args.lb_side)
+        if "ensemble" in parts:
+            extra["ensemble"] = measure_ensemble(torch, B, dev)
+        if "serving" in parts:
+            extra["serving"] = measure_serving(B)
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:

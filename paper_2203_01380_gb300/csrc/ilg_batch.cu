@@ -99,12 +99,12 @@ __device__ __forceinline__ longlong2 trig_fixed(uint32_t r, uint32_t L) {
 // Lmax apart): with D(x) = L N(x) - M and r = (m x) mod L,
 //   re = sum_x cos(2 pi r / L) D(x) / L,  im = sum_x sin(2 pi r / L) D(x) / L.
 // The trigonometric values enter as 2^-62 fixed-point integers (from trig, indexed
-// by x, when given) and the sums are exact in 128-bit integers, so the result is
-// independent of the summation order and rounded once.  Valid in thread 0; every
-// thread must call it.
+// by x, when given) and the sums are exact in 128-bit integers, so they do not
+// depend on the summation order.  ring_partials: every warp reduces its nodes and
+// its lane 0 stores (re.lo, re.hi, im.lo, im.hi) at red[4 warp ..]; no barrier.
 template <int THREADS>
-__device__ void ring_projection(const uint16_t* buf, uint32_t L, uint32_t Lmax, uint64_t mass, uint32_t m,
-                                const longlong2* trig, unsigned long long* red, double& re, double& im) {
+__device__ void ring_partials(const uint16_t* buf, uint32_t L, uint32_t Lmax, uint64_t mass, uint32_t m,
+                              const longlong2* trig, unsigned long long* red) {
   I128 ac, as;
   for (uint32_t x = threadIdx.x; x < L; x += THREADS) {
     const long long N = (long long)buf[x] + buf[Lmax + x] + buf[2 * Lmax + x];
@@ -122,24 +122,28 @@ __device__ void ring_projection(const uint16_t* buf, uint32_t L, uint32_t Lmax, 
     ac.add(cl, ch);
     as.add(sl, sh);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[4 * warp + 0] = ac.lo;
-    red[4 * warp + 1] = (unsigned long long)ac.hi;
-    red[4 * warp + 2] = as.lo;
-    red[4 * warp + 3] = (unsigned long long)as.hi;
+  if ((threadIdx.x & 31) == 0) {
+    const int w = threadIdx.x >> 5;
+    red[4 * w + 0] = ac.lo;
+    red[4 * w + 1] = (unsigned long long)ac.hi;
+    red[4 * w + 2] = as.lo;
+    red[4 * w + 3] = (unsigned long long)as.hi;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    I128 c, s;
-    for (int w = 0; w < THREADS / 32; ++w) {
-      c.add(red[4 * w + 0], (long long)red[4 * w + 1]);
-      s.add(red[4 * w + 2], (long long)red[4 * w + 3]);
-    }
-    re = i128_to_double_2m62(c) / double(L);
-    im = i128_to_double_2m62(s) / double(L);
+}
+
+// Sum of the warps' partials (one thread): the raw 128-bit sums of re and im
+// (times L 2^62) go to out[0..3].
+template <int THREADS>
+__device__ void ring_finalise(const unsigned long long* red, long long* out) {
+  I128 c, s;
+  for (int w = 0; w < THREADS / 32; ++w) {
+    c.add(red[4 * w + 0], (long long)red[4 * w + 1]);
+    s.add(red[4 * w + 2], (long long)red[4 * w + 3]);
   }
-  __syncthreads();
+  out[0] = (long long)c.lo;
+  out[1] = c.hi;
+  out[2] = (long long)s.lo;
+  out[3] = s.hi;
 }
 
 template <int THREADS>
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
   __shared__ uint32_t s_task;
   __shared__ int s_fail;
   __shared__ unsigned long long s_mass;
-  __shared__ unsigned long long s_red[4 * (THREADS / 32)];
+  __shared__ unsigned long long s_red[2][4 * (THREADS / 32)];   // projection partials, by state parity
   const int tid = threadIdx.x;
 
   for (;;) {
@@ -195,13 +199,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
       if (part) atomicAdd(&s_mass, part);
       __syncthreads();
       mass = s_mass;
-      double re, im;
-      ring_projection<THREADS>(buf0, L, b.Lmax, mass, mrec, b.trig, s_red, re, im);
-      if (tid == 0) {
-        double* o = b.record + size_t(r) * (b.T + 1) * 2;
-        o[0] = re;
-        o[1] = im;
-      }
+      // partials of state 0 into slot 0 (finalised after the first step's barrier)
+      ring_partials<THREADS>(buf0, L, b.Lmax, mass, mrec, b.trig, s_red[0]);
     }
 
     uint16_t* src = buf0;
@@ -234,15 +233,15 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
       dst = tmp;
       steps_done = s + 1;
       if (rec) {
-        // complex amplitude of the new state (t + 1)
-        double re, im;
-        ring_projection<THREADS>(src, L, b.Lmax, mass, mrec, b.trig, s_red, re, im);
-        if (tid == 0) {
-          double* o = b.record + (size_t(r) * (b.T + 1) + s + 1) * 2;
-          o[0] = re;
-          o[1] = im;
-        }
+        // state s was reduced into slot s & 1 before this step's barrier: finalise
+        // it; then the warps reduce the new state s + 1 into the other slot
+        if (tid == 0) ring_finalise<THREADS>(s_red[s & 1], b.record + (size_t(r) * (b.T + 1) + s) * 4);
+        ring_partials<THREADS>(src, L, b.Lmax, mass, mrec, b.trig, s_red[(s + 1) & 1]);
       }
+    }
+    if (rec && s_fail < 0) {
+      __syncthreads();
+      if (tid == 0) ring_finalise<THREADS>(s_red[b.T & 1], b.record + (size_t(r) * (b.T + 1) + b.T) * 4);
     }
     // ring back to global memory; the replica's step counter moves on
     uint16_t* gd = b.state + d.state_off;
@@ -337,6 +336,24 @@ __global__ void batch_trig_kernel(uint32_t L, uint32_t m, longlong2* __restrict_
     trig[x] = trig_fixed(uint32_t((uint64_t(m) * x) % L), L);
 }
 
+// Raw 128-bit sums (L 2^62 re, L 2^62 im) -> (re, im) in double, rounded once and
+// divided by L.
+__global__ void batch_convert_kernel(const ReplicaDesc* __restrict__ desc, const long long* __restrict__ raw,
+                                     uint32_t n, uint32_t T, double* __restrict__ rec) {
+  const size_t total = size_t(n) * (T + 1);
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+    const double L = double(desc[i / (T + 1)].L);
+    const long long* v = raw + 4 * i;
+    I128 re, im;
+    re.lo = (unsigned long long)v[0];
+    re.hi = v[1];
+    im.lo = (unsigned long long)v[2];
+    im.hi = v[3];
+    rec[2 * i] = i128_to_double_2m62(re) / L;
+    rec[2 * i + 1] = i128_to_double_2m62(im) / L;
+  }
+}
+
 // amp[r T + s] = im / (L_r / 2) of the record entry after step s.
 __global__ void batch_amp_kernel(const ReplicaDesc* __restrict__ desc, const double* __restrict__ record,
                                  uint32_t n, uint32_t T, double* __restrict__ amp) {
@@ -413,6 +430,14 @@ cudaError_t launch_batch_amp(const ReplicaDesc* desc, const double* record, uint
   const size_t total = size_t(n) * T;
   const int grid = int(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096);
   batch_amp_kernel<<<grid, 256, 0, s>>>(desc, record, n, T, amp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_convert(const ReplicaDesc* desc, const long long* raw, uint32_t n, uint32_t T, double* rec,
+                                 cudaStream_t s) {
+  const size_t total = size_t(n) * (T + 1);
+  const int grid = int(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096);
+  batch_convert_kernel<<<grid, 256, 0, s>>>(desc, raw, n, T, rec);
   return cudaGetLastError();
 }
 

@@ -36,8 +36,9 @@ struct BatchArgs {
   uint16_t* state;
   unsigned int* counter;   // work queue head, 0 at launch
   uint32_t* failed;        // per replica: 1 when a step would exceed 65535
-  double* record;          // n x (T + 1) x (re, im) of the recorded mode: at the launch's
-                           // start, then after every step; or NULL
+  long long* record;       // n x (T + 1) x 4: exact sums (L 2^62 re, L 2^62 im) as 128-bit
+                           // (lo, hi) pairs of the recorded mode at the launch's start, then
+                           // after every step; or NULL
   const longlong2* trig;   // fixed-point (cos, sin) of the recorded mode indexed by x when
                            // every ring has one length, else NULL (computed per node)
 };
@@ -49,6 +50,8 @@ cudaError_t launch_batch_obs(const ReplicaDesc* desc, const uint16_t* state, uin
                              unsigned long long* mass, double* amp, cudaStream_t s);
 cudaError_t launch_batch_amp(const ReplicaDesc* desc, const double* record, uint32_t n, uint32_t T, double* amp,
                              cudaStream_t s);
+cudaError_t launch_batch_convert(const ReplicaDesc* desc, const long long* raw, uint32_t n, uint32_t T, double* rec,
+                                 cudaStream_t s);
 cudaError_t launch_batch_trig(uint32_t L, int32_t mode, longlong2* trig, cudaStream_t s);
 cudaError_t launch_batch_ensemble(const double* record, uint32_t n, uint32_t T, double* out, cudaStream_t s);
 

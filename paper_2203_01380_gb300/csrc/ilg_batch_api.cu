@@ -31,8 +31,10 @@ struct ilg_batch {
   uint32_t* d_order = nullptr;
   unsigned int* d_counter = nullptr;
   uint32_t* d_failed = nullptr;
-  double* d_record = nullptr;
+  long long* d_record = nullptr;      // raw 128-bit amplitude sums, n x (T + 1) x 4
   size_t record_cap = 0;
+  double* d_rec = nullptr;            // the same as (re, im) doubles, n x (T + 1) x 2
+  size_t rec_cap = 0;
   double* d_out = nullptr;            // amplitude record or ensemble statistics
   size_t out_cap = 0;
   longlong2* d_trig = nullptr;        // fixed-point trigonometric table of the ensemble mode
@@ -84,6 +86,7 @@ void free_batch(ilg_batch* b) {
   cudaFree(b->d_counter);
   cudaFree(b->d_failed);
   cudaFree(b->d_record);
+  cudaFree(b->d_rec);
   cudaFree(b->d_out);
   cudaFree(b->d_trig);
   cudaFree(b->d_mass);
@@ -262,17 +265,17 @@ namespace {
 // Queue one persistent launch of T steps (graph-captured, re-captured when T, the
 // record flag or the mode change) and the read-back of the per-ring flags and
 // descriptors.  With rec the complex amplitude of record_mode is recorded at the
-// start and after every step (n x (T + 1) x 2 doubles in d_record).
+// start and after every step (n x (T + 1) x 4 raw 128-bit sums in d_record).
 ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec, bool trig,
                         std::vector<uint32_t>& failed) {
   for (const auto& d : b->desc)
     if (uint64_t(d.t) + T >= (uint64_t(1) << 32)) return bfail(b, ILG_E_INVALID, "step counter would reach 2^32");
-  const size_t need = size_t(b->n) * (size_t(T) + 1) * 2;
+  const size_t need = size_t(b->n) * (size_t(T) + 1) * 4;
   if (rec && b->record_cap < need) {
     cudaFree(b->d_record);
     b->d_record = nullptr;
     b->record_cap = 0;
-    BCUDA(b, cudaMalloc(&b->d_record, sizeof(double) * need), "cudaMalloc record");
+    BCUDA(b, cudaMalloc(&b->d_record, sizeof(long long) * need), "cudaMalloc record");
     b->record_cap = need;
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
@@ -372,13 +375,15 @@ ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* 
   const bool rec = amp_record != nullptr;
   std::vector<uint32_t> failed;
   if (rec) {
-    const ilg_status st = ensure_doubles(b, &b->d_out, &b->out_cap, size_t(b->n) * T);
+    ilg_status st = ensure_doubles(b, &b->d_out, &b->out_cap, size_t(b->n) * T);
+    if (st == ILG_OK) st = ensure_doubles(b, &b->d_rec, &b->rec_cap, size_t(b->n) * (size_t(T) + 1) * 2);
     if (st != ILG_OK) return st;
   }
   ilg_status st = batch_launch(b, T, record_mode, rec, false, failed);
   if (st != ILG_OK) return st;
   if (rec) {
-    BCUDA(b, launch_batch_amp(b->d_desc, b->d_record, b->n, T, b->d_out, b->stream), "amplitude record");
+    BCUDA(b, launch_batch_convert(b->d_desc, b->d_record, b->n, T, b->d_rec, b->stream), "convert record");
+    BCUDA(b, launch_batch_amp(b->d_desc, b->d_rec, b->n, T, b->d_out, b->stream), "amplitude record");
     BCUDA(b, cudaMemcpyAsync(amp_record, b->d_out, sizeof(double) * b->n * size_t(T), cudaMemcpyDeviceToHost, b->stream),
           "read record");
   }
@@ -393,15 +398,17 @@ ilg_status ilg_batch_ensemble(ilg_batch* b, uint32_t T, int32_t mode, double* st
     if (d.L != b->desc[0].L) return bfail(b, ILG_E_INVALID, "ensemble statistics need rings of one length");
   if (mode % int64_t(b->desc[0].L) == 0) return bfail(b, ILG_E_INVALID, "the mode must not be a multiple of L");
   ilg_status st = ensure_doubles(b, &b->d_out, &b->out_cap, 6 * (size_t(T) + 1));
+  if (st == ILG_OK) st = ensure_doubles(b, &b->d_rec, &b->rec_cap, size_t(b->n) * (size_t(T) + 1) * 2);
   if (st != ILG_OK) return st;
   std::vector<uint32_t> failed;
   st = batch_launch(b, T, mode, true, true, failed);
   if (st != ILG_OK) return st;
-  BCUDA(b, launch_batch_ensemble(b->d_record, b->n, T, b->d_out, b->stream), "ensemble statistics");
+  BCUDA(b, launch_batch_convert(b->d_desc, b->d_record, b->n, T, b->d_rec, b->stream), "convert record");
+  BCUDA(b, launch_batch_ensemble(b->d_rec, b->n, T, b->d_out, b->stream), "ensemble statistics");
   BCUDA(b, cudaMemcpyAsync(stats, b->d_out, sizeof(double) * 6 * (size_t(T) + 1), cudaMemcpyDeviceToHost, b->stream),
         "read statistics");
   if (record)
-    BCUDA(b, cudaMemcpyAsync(record, b->d_record, sizeof(double) * 2 * b->n * (size_t(T) + 1), cudaMemcpyDeviceToHost,
+    BCUDA(b, cudaMemcpyAsync(record, b->d_rec, sizeof(double) * 2 * b->n * (size_t(T) + 1), cudaMemcpyDeviceToHost,
                              b->stream),
           "read record");
   return batch_finish(b, failed);
