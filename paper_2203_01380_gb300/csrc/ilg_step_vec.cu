@@ -97,14 +97,11 @@ struct FastCollide {
 
 // collide one node (occupations m, already flipped) on the fast path (no result
 // there exceeds 65535); returns false when the node needs the general collision
-// (post is then 0)
+// (post is then undefined: the general pass overwrites the node's half-words)
 template <int Q, class Coll>
 __device__ __forceinline__ bool node_update(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
                                             const uint32_t (&m)[Q], uint32_t (&post)[Q]) {
-  const bool ok = Coll::template run<Q>(a, s, node, t, m, post);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) post[i] = ok ? post[i] : 0u;
-  return ok;
+  return Coll::template run<Q>(a, s, node, t, m, post);
 }
 
 template <int Q, int NPT, bool UNROLL, int MINB, class Coll = FastCollide, int THREADS = kVecThreads>
@@ -172,7 +169,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
             if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + k, t, n, post)) slow |= 1u << k;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-              if (k & 1) P[i].w[k >> 1] |= post[i] << 16;
+              if (k & 1) P[i].w[k >> 1] = __byte_perm(P[i].w[k >> 1], post[i], 0x5410);
               else P[i].w[k >> 1] = post[i];
             }
           }
@@ -190,7 +187,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
               if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + 2 * j + h, t, n, post))
                 slow |= 1u << (2 * j + h);
 #pragma unroll
-              for (int i = 0; i < Q; ++i) acc[i] = h ? (acc[i] | (post[i] << 16)) : post[i];
+              for (int i = 0; i < Q; ++i) acc[i] = h ? __byte_perm(acc[i], post[i], 0x5410) : post[i];
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -220,7 +217,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
             const uint32_t v = post[i] & 0xFFFFu;
 #pragma unroll
             for (int kk = 0; kk < NPT; ++kk)
-              if (kk == k) P[i].w[kk >> 1] |= v << (16 * (kk & 1));
+              if (kk == k) {
+                const uint32_t sh = 16 * (kk & 1);
+                P[i].w[kk >> 1] = (P[i].w[kk >> 1] & ~(0xFFFFu << sh)) | (v << sh);
+              }
           }
         }
         vstore<NPT>(out + rowoff + x0, P[0]);
