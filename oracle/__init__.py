@@ -57,6 +57,7 @@ class _StepParams(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("replica", ctypes.c_uint32),
         ("thr_omega", ctypes.c_void_p), ("alias_omega", ctypes.c_void_p),
         ("thr_rest", ctypes.c_void_p), ("alias_rest", ctypes.c_void_p),
+        ("sampler", ctypes.c_int32),
     ]
 
 
@@ -105,6 +106,9 @@ def lib():
         L.oracle_collide_many.argtypes = [ctypes.POINTER(_StepParams), u32p, ctypes.c_uint32,
                                           ctypes.c_uint32, ctypes.c_uint32, u32p]
         L.oracle_collide_many.restype = None
+        L.oracle_particle_bounds.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
+                                             np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")]
+        L.oracle_particle_bounds.restype = None
         _lib = L
     return _lib
 
@@ -164,6 +168,13 @@ def poisson_table(lam: float) -> np.ndarray:
     return T[:K].copy()
 
 
+def particle_bounds(lattice: int, P_omega: int, P_rest: int) -> list:
+    """Boundaries B_0..B_Q of the particle sampler (one word per particle)."""
+    B = np.zeros(6, dtype=np.uint64)
+    lib().oracle_particle_bounds(lattice, P_omega, P_rest, B)
+    return [int(b) for b in B[:num_vel(lattice) + 1]]
+
+
 def philox(ctr, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib().oracle_philox(np.asarray(ctr, dtype=np.uint32), np.asarray(key, dtype=np.uint32), out)
@@ -174,8 +185,9 @@ class Lattice:
     """Parameters of one lattice, as the library's ilg_params carries them."""
 
     def __init__(self, lattice, Lx, Ly=1, n0=10.0, amp=0.0, mode_mx=0, mode_my=0,
-                 init_weighted=0, omega_eff=1.0, theta=1.0 / 3.0, seed=0, replica=0):
+                 init_weighted=0, omega_eff=1.0, theta=1.0 / 3.0, seed=0, replica=0, sampler=0):
         self.lattice, self.Lx, self.Ly = lattice, int(Lx), int(Ly if lattice == D2Q5 else 1)
+        self.sampler = int(sampler)   # 0: binomial draws through alias tables; 1: one word per particle
         self.n0, self.amp, self.mode_mx, self.mode_my = float(n0), float(amp), mode_mx, mode_my
         self.init_weighted, self.omega_eff, self.theta = init_weighted, float(omega_eff), float(theta)
         self.seed, self.replica = int(seed), int(replica)
@@ -191,7 +203,7 @@ class Lattice:
     def _sp(self):
         return _StepParams(self.lattice, self.Lx, self.Ly, self.flip, self.P_omega, self.P_rest,
                            self.seed, self.replica, self._A_omega[0].ctypes.data, self._A_omega[1].ctypes.data,
-                           self._A_rest[0].ctypes.data, self._A_rest[1].ctypes.data)
+                           self._A_rest[0].ctypes.data, self._A_rest[1].ctypes.data, self.sampler)
 
     def _ip(self):
         return _InitParams(self.lattice, self.Lx, self.Ly, self.n0, self.amp, self.mode_mx,

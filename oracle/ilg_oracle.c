@@ -42,6 +42,7 @@
 #define OR_TAG_STEP 1u
 #define OR_TAG_EXT 2u
 #define OR_TAG_INIT 3u
+#define OR_TAG_PARTICLE 4u
 #define OR_POISSON_KMAX 4096u
 
 /* ------------------------------------------------------------------------ */
@@ -192,6 +193,7 @@ typedef struct {
   const uint8_t *alias_omega;
   const uint32_t *thr_rest;  /* alias table of P_rest (unused if P_rest is 0 or 2^32) */
   const uint8_t *alias_rest;
+  int32_t sampler;           /* 0: binomial draws (collide_node); 1: one word per particle */
 } oracle_step_params;
 
 static int num_vel(int32_t lattice) { return lattice == 1 ? 3 : 5; }
@@ -285,6 +287,66 @@ static void collide_node(const oracle_step_params *p, uint32_t node, uint32_t t,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Particle sampler: every particle decides on its own word                  */
+/* ------------------------------------------------------------------------ */
+/*
+ * The same law as above, drawn the plain way (Sec. II: each particle is picked
+ * with probability omega* and a picked particle goes to velocity j with
+ * probability w_j).  One 32-bit word u per particle, from the tag-4 stream of
+ * the node, in particle order (velocity 0..Q-1 of the flipped occupation, then
+ * particle 0..m_i-1).  The word is compared with integer boundaries
+ *   B_0     = 2^32 - P_omega                      (below: the particle stays)
+ *   B_{j+1} = B_0 + floor(P_omega (P_rest (Q-1) + j (2^32 - P_rest)) / ((Q-1) 2^32))
+ * for j = 0..Q-1 (B_Q = 2^32): a particle with B_j <= u < B_{j+1} goes to
+ * velocity j.  Picked with probability P_omega / 2^32; then rest with P_rest / 2^32
+ * and each moving velocity with an equal share of the remainder (to within one
+ * unit of 2^-32 per boundary).
+ */
+static void particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t *B) {
+  const unsigned __int128 two32 = (unsigned __int128)1 << 32;
+  B[0] = (uint64_t)(two32 - P_omega);
+  for (int j = 0; j < Q; ++j) {
+    unsigned __int128 num = (unsigned __int128)P_omega *
+                            ((unsigned __int128)P_rest * (unsigned)(Q - 1) + (unsigned __int128)j * (two32 - P_rest));
+    unsigned __int128 den = (unsigned __int128)(unsigned)(Q - 1) << 32;
+    B[j + 1] = B[0] + (uint64_t)(num / den);
+  }
+}
+
+static void collide_node_particle(const oracle_step_params *p, uint32_t node, uint32_t t,
+                                  const uint32_t *m, uint32_t *out) {
+  int Q = num_vel(p->lattice);
+  uint64_t B[6];
+  particle_bounds(Q, p->P_omega, p->P_rest, B);
+  for (int i = 0; i < Q; ++i) out[i] = 0;
+  uint32_t d = 0;
+  for (int i = 0; i < Q; ++i) {
+    for (uint32_t k = 0; k < m[i]; ++k) {
+      uint64_t u = stream_word(p->seed, node, t, p->replica, OR_TAG_PARTICLE, d);
+      d += 1;
+      if (u < B[0]) {
+        out[i] += 1;
+      } else {
+        int j = 0;
+        while (u >= B[j + 1]) j += 1;
+        out[j] += 1;
+      }
+    }
+  }
+}
+
+static void collide_any(const oracle_step_params *p, uint32_t node, uint32_t t, const uint32_t *m,
+                        uint32_t *out) {
+  if (p->sampler == 1) collide_node_particle(p, node, t, m, out);
+  else collide_node(p, node, t, m, out);
+}
+
+/* exported for the tests: the boundaries B_0..B_Q */
+void oracle_particle_bounds(int32_t lattice, uint64_t P_omega, uint64_t P_rest, uint64_t *B) {
+  particle_bounds(num_vel(lattice), P_omega, P_rest, B);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Time step over a rectangular region                                       */
 /* ------------------------------------------------------------------------ */
 /*
@@ -312,7 +374,7 @@ int oracle_step_region(const oracle_step_params *p, const uint16_t *in, uint16_t
       uint32_t n[5], m[5], post[5];
       for (int v = 0; v < Q; ++v) n[v] = in[v * plane + (size_t)j * w + i];
       for (int v = 0; v < Q; ++v) m[v] = p->flip ? n[OPP[v]] : n[v];
-      collide_node(p, node, t, m, post);
+      collide_any(p, node, t, m, post);
       for (int v = 0; v < Q; ++v) {
         if (post[v] > 65535u) return 3;
         long di = (long)i + VX[v];
@@ -453,5 +515,5 @@ void oracle_sums(int32_t lattice, uint32_t Lx, uint32_t Ly, const uint16_t *stat
 void oracle_collide_many(const oracle_step_params *p, const uint32_t *m, uint32_t t,
                          uint32_t node0, uint32_t count, uint32_t *out) {
   int Q = num_vel(p->lattice);
-  for (uint32_t k = 0; k < count; ++k) collide_node(p, node0 + k, t, m, out + (size_t)k * Q);
+  for (uint32_t k = 0; k < count; ++k) collide_any(p, node0 + k, t, m, out + (size_t)k * Q);
 }

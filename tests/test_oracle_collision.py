@@ -171,3 +171,60 @@ def test_paper_transform_is_hermite_orthogonal_with_weights():
     ow = O.weights(O.D1Q3, 0.25)
     assert ow == [0.75, 0.125, 0.125]
     assert O.weights(O.D2Q5, 1.0 / 3.0)[0] == pytest.approx(1.0 / 3.0)
+
+
+# ---------------------------------------------------------------- particle sampler
+# The plain per-particle form of the same collision: one word per particle against
+# integer boundaries.  Its law must be the paper's (Sec. II) to within the 2^-32
+# quantisation, so it is compared with the same exact enumeration.
+
+@pytest.mark.parametrize("lattice,omega,theta", [(O.D1Q3, 0.3, 1 / 3), (O.D1Q3, 1.0, 0.6), (O.D2Q5, 0.45, 1 / 3),
+                                                 (O.D2Q5, 0.0, 0.4), (O.D2Q5, 1.0, 0.2)])
+def test_particle_bounds_realise_the_law(lattice, omega, theta):
+    lat = O.Lattice(lattice, 8, 8, omega_eff=omega, theta=theta)
+    B = O.particle_bounds(lattice, lat.P_omega, lat.P_rest)
+    Q = lat.Q
+    assert len(B) == Q + 1 and B[-1] == 1 << 32
+    assert all(B[k] <= B[k + 1] for k in range(Q))
+    w = O.weights(lattice, theta)
+    two32 = float(1 << 32)
+    assert abs(B[0] / two32 - (1 - omega)) <= 1.5 / two32
+    for j in range(Q):
+        assert abs((B[j + 1] - B[j]) / two32 - omega * w[j]) <= 3 / two32, j
+
+
+@pytest.mark.parametrize("lattice,m,omega,theta", CASES)
+def test_particle_sampler_law_exact(lattice, m, omega, theta):
+    lat = O.Lattice(lattice, 16, 16, omega_eff=omega, theta=theta, seed=23 + sum(m), sampler=1)
+    law = exact_law(lat, m)
+    out = lat.collide_many(m, t=3, node0=0, count=200_000)
+    assert np.all(out.sum(axis=1) == sum(m))
+    assert chi2_pvalue(out, law) > 1e-4
+
+
+@pytest.mark.parametrize("lattice,m,omega", [(O.D2Q5, (300, 70, 0, 45, 200), 0.5), (O.D1Q3, (150, 260, 90), 0.8)])
+def test_particle_sampler_moments_large(lattice, m, omega):
+    lat = O.Lattice(lattice, 16, 16, omega_eff=omega, seed=6, sampler=1)
+    P = np.array([[float(v) for v in row] for row in transition(lat)])
+    mm = np.array(m, float)
+    mean = mm @ P
+    cov = -np.einsum("i,ij,ik->jk", mm, P, P) + np.diag(mm @ P)
+    n = 30_000
+    out = lat.collide_many(m, t=2, node0=7, count=n).astype(float)
+    assert np.all(out.sum(axis=1) == sum(m))
+    z = (out.mean(axis=0) - mean) / np.sqrt(np.diag(cov) / n)
+    assert np.all(np.abs(z) < 5), z
+
+
+def test_particle_sampler_special_cases():
+    """omega* = 0 keeps every particle (Sec. V: the pure flip); the two samplers differ
+    in their bits but not in mass."""
+    m = (7, 3, 0, 11, 2)
+    keep = O.Lattice(O.D2Q5, 8, 8, omega_eff=2.0, seed=1, sampler=1)
+    assert keep.P_omega == 0
+    out = keep.collide_many(m, t=0, node0=0, count=50)
+    assert np.all(out == np.array(m))
+    a = O.Lattice(O.D2Q5, 8, 8, omega_eff=0.7, seed=1, sampler=1).collide_many(m, t=0, node0=0, count=50)
+    b = O.Lattice(O.D2Q5, 8, 8, omega_eff=0.7, seed=1, sampler=0).collide_many(m, t=0, node0=0, count=50)
+    assert not np.array_equal(a, b)
+    assert np.all(a.sum(axis=1) == sum(m)) and np.all(b.sum(axis=1) == sum(m))

@@ -141,10 +141,12 @@ def test_long_wave_decay_rate(omega_j):
     assert abs(rate / (D * k * k) - 1) < 1e-3
 
 
-def test_lattice_gas_mean_is_lattice_boltzmann():
-    """Replica mean of the integer lattice gas (oracle) after a few steps from a
-    Poisson start against the lattice Boltzmann state from the Poisson means."""
-    cfg = dict(n0=12.0, amp=9.0, mode_mx=1, init_weighted=1, omega_eff=1.6, seed=17)
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_lattice_gas_mean_is_lattice_boltzmann(sampler):
+    """Replica mean of the integer lattice gas (oracle, either sampler) after a few
+    steps from a Poisson start against the lattice Boltzmann state from the Poisson
+    means."""
+    cfg = dict(n0=12.0, amp=9.0, mode_mx=1, init_weighted=1, omega_eff=1.6, seed=17, sampler=sampler)
     Lx, T, R = 16, 6, 600
     oj, om = L.rates_from_omega_eff(cfg["omega_eff"])
     lb = L.LB(O.D1Q3, Lx, omega_j=oj, omega=om)
