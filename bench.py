@@ -272,6 +272,27 @@ def measure_ensemble(torch, B, dev):
             "structure_factor_t0_over_mass": float(stats["cov_re"][0] / (cfg["n0"] * 3 * L))}
 
 
+def measure_particle(torch, B, dev, side):
+    """The main workload with the particle (reference) sampler: one word per particle."""
+    cfg = {k: v for k, v in inputs.LARGE_D2Q5.items() if k != "steps"}
+    cfg.update(Lx=side, Ly=side, sampler=B.SAMPLER_PARTICLE)
+    st = torch.cuda.Stream(dev)
+    T = 20
+    with B.Lattice(**cfg, stream=st) as lat:
+        lat.init()
+        lat.step(2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        lat.step(T)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / T
+    return {"workload": f"large_d2q5 with the particle sampler: D2Q5 {side}x{side}, {T} steps",
+            "value": side * side / (ms / 1e3) / 1e9, "unit": "GNUPS", "ms_per_step": ms,
+            "kernel": "step_kernel<5> (general path, one Philox word per particle)"}
+
+
 def serve_stream(B, reqs, slots, smallest_first):
     """Submit requests at their arrival times; returns results, wall time, stats."""
     with B.Server(5, 48 << 30, max_slots=slots, quantum=32) as srv:
@@ -371,7 +392,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip every measurement beyond the main workload")
-    ap.add_argument("--extra", default="tb,batched,lb,ensemble,serving",
+    ap.add_argument("--extra", default="tb,batched,lb,ensemble,particle,serving",
                     help="comma-separated measurements beyond the main workload")
     ap.add_argument("--lb-side", type=int, default=0, help="side of the lattice Boltzmann workload (default 16384)")
     args = ap.parse_args()
@@ -481,6 +502,8 @@ def main():
             extra["lattice_boltzmann"] = measure_lb(torch, B, dev, clk.summary(), args.lb_side)
         if "ensemble" in parts:
             extra["ensemble"] = measure_ensemble(torch, B, dev)
+        if "particle" in parts:
+            extra["particle_sampler"] = measure_particle(torch, B, dev, args.side)
         if "serving" in parts:
             extra["serving"] = measure_serving(B)
 

@@ -61,7 +61,15 @@ typedef enum { ILG_D1Q3 = 1, ILG_D2Q5 = 2 } ilg_lattice;
  *                  > 1 flip on and omega* = 2 - omega_eff, so omega^j = omega_eff
  *   theta          D1Q3 weights (1-theta, theta/2, theta/2), theta in (0, 1);
  *                  D2Q5 weights (1-2 theta, theta/2 x4), theta in (0, 1/2]
- *   seed, replica  Philox key and the replica word of every counter */
+ *   seed, replica  Philox key and the replica word of every counter
+ *   sampler        how the collision draws its random decisions (same law, different bits):
+ *                  ILG_SAMPLER_BINOMIAL (0): per velocity one binomial draw of the
+ *                    particles removed, one of those sent to rest, and one bit per
+ *                    moving particle for its direction; each draw is one 32-bit word
+ *                    through an integer alias table (the fast sampler)
+ *                  ILG_SAMPLER_PARTICLE (1): every particle decides on its own
+ *                    32-bit word against integer boundaries (stay, rest, each moving
+ *                    velocity): the plain reference form, one word per particle */
 typedef struct {
   int32_t lattice;
   uint32_t Lx;
@@ -75,8 +83,10 @@ typedef struct {
   double theta;
   uint64_t seed;
   uint32_t replica;
-  uint32_t reserved; /* must be 0 */
+  uint32_t sampler;  /* ILG_SAMPLER_BINOMIAL or ILG_SAMPLER_PARTICLE */
 } ilg_params;
+
+enum { ILG_SAMPLER_BINOMIAL = 0, ILG_SAMPLER_PARTICLE = 1 };
 
 typedef struct ilg_ctx ilg_ctx;
 

@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
         ("mode_mx", ctypes.c_int32), ("mode_my", ctypes.c_int32), ("init_weighted", ctypes.c_int32),
         ("n0", ctypes.c_double), ("amp", ctypes.c_double), ("omega_eff", ctypes.c_double),
         ("theta", ctypes.c_double), ("seed", ctypes.c_uint64), ("replica", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("sampler", ctypes.c_uint32),
     ]
 
 
@@ -126,11 +126,14 @@ def _check(status: int, ctx=None):
         raise IlgError(status, msg)
 
 
+SAMPLER_BINOMIAL, SAMPLER_PARTICLE = 0, 1
+
+
 def make_params(lattice, Lx, Ly=1, n0=10.0, amp=0.0, mode_mx=0, mode_my=0, init_weighted=0,
-                omega_eff=1.0, theta=1.0 / 3.0, seed=0, replica=0, **_ignored) -> Params:
+                omega_eff=1.0, theta=1.0 / 3.0, seed=0, replica=0, sampler=0, **_ignored) -> Params:
     return Params(int(lattice), int(Lx), int(Ly if lattice == D2Q5 else 1), int(mode_mx), int(mode_my),
                   int(init_weighted), float(n0), float(amp), float(omega_eff), float(theta), int(seed),
-                  int(replica), 0)
+                  int(replica), int(sampler))
 
 
 class Lattice:

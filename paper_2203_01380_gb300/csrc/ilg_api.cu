@@ -76,7 +76,8 @@ uint32_t prob_mode(uint64_t P) {
 namespace ilg {
 std::string validate_params(const ilg_params& p) {
   if (p.lattice != ILG_D1Q3 && p.lattice != ILG_D2Q5) return "lattice must be ILG_D1Q3 or ILG_D2Q5";
-  if (p.reserved != 0) return "reserved field must be 0";
+  if (p.sampler != ILG_SAMPLER_BINOMIAL && p.sampler != ILG_SAMPLER_PARTICLE)
+    return "sampler must be ILG_SAMPLER_BINOMIAL or ILG_SAMPLER_PARTICLE";
   const uint64_t Ly = p.lattice == ILG_D1Q3 ? 1 : p.Ly;
   if (p.Lx < 3) return "Lx must be >= 3";
   if (p.lattice == ILG_D2Q5 && p.Ly < 3) return "Ly must be >= 3";
@@ -126,7 +127,8 @@ StepArgs step_args(const ilg_ctx* c) {
   a.flip = c->flip;
   a.omega_mode = prob_mode(c->P_omega);
   a.rest_mode = prob_mode(c->P_rest);
-  a.general = c->general;
+  a.particle = c->p.sampler == ILG_SAMPLER_PARTICLE ? 1u : 0u;
+  a.general = c->general | a.particle;
   a.key0 = uint32_t(c->p.seed);
   a.key1 = uint32_t(c->p.seed >> 32);
   a.replica = c->p.replica;
@@ -209,9 +211,7 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
   if ((e = cudaMallocHost(&c->h_word, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMallocHost");
 
   std::vector<uint32_t> tables(kBlockWords, 0u);
-  AliasEntry* alias = reinterpret_cast<AliasEntry*>(tables.data());
-  if (prob_mode(c->P_omega) == kTable) build_alias_table(c->P_omega, alias);
-  if (prob_mode(c->P_rest) == kTable) build_alias_table(c->P_rest, alias + kAliasEntries);
+  build_table_block(c->Q, c->p.sampler, c->P_omega, c->P_rest, tables.data());
   if ((e = prepare_step_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   if ((e = prepare_step_vec_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   e = cudaMemcpyAsync(c->d_tables, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice, c->stream);
@@ -351,8 +351,9 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   if (c->t + T >= (uint64_t(1) << 32)) return fail(c, ILG_E_INVALID, "step counter would reach 2^32");
   if (T == 0) return ILG_OK;
   const StepArgs a = step_args(c);
-  // high occupations go straight to the general collision (node-parallel kernel)
-  const bool vec = !c->general && (c->p.Lx % step_vec_width()) == 0;
+  // high occupations and the particle sampler go straight to the general collision
+  // (node-parallel kernel)
+  const bool vec = !a.general && (c->p.Lx % step_vec_width()) == 0;
   const int grid = vec ? vec_grid(c) : step_grid(c, 3);
   const int cur0 = c->cur;
   const uint64_t t0 = c->t;

@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
     a.rest_mode = d.rest_mode;
     a.replica = d.replica;
     a.general = d.general;
+    a.particle = d.particle;
 
     // tables and ring into shared memory
     const uint4* gt = reinterpret_cast<const uint4*>(b.tables + size_t(r) * kDevBlockWords);
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
         m[1] = a.flip ? n[2] : n[1];
         m[2] = a.flip ? n[1] : n[2];
         if (a.general || !collide_try_fast<3>(a, tables, x, t, m, post)) {
-          collide_phased<3, kBatchExtWords, THREADS>(a, tables, x, t, m, post, xbuf + tid);
+          collide_general<3, kBatchExtWords, THREADS>(a, tables, x, t, m, post, xbuf + tid);
           bad |= post[0] > 65535u || post[1] > 65535u || post[2] > 65535u;
         }
         const uint32_t xp = x + 1 == L ? 0 : x + 1;

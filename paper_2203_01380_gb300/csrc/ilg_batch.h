@@ -20,8 +20,8 @@ struct ReplicaDesc {
   uint32_t rest_mode;
   uint32_t replica;     // replica word of the Philox counter
   uint32_t t;           // step counter (advanced by the kernel)
-  uint32_t general;     // 1: skip the fast path (high occupation)
-  uint32_t pad;
+  uint32_t general;     // 1: skip the fast path (high occupation or particle sampler)
+  uint32_t particle;    // 1: particle sampler
   uint64_t state_off;   // first of the replica's 3 L occupations in the batch buffer
 };
 

@@ -14,6 +14,7 @@ constexpr uint32_t kDevBlockWords = 2 * kDevAliasEntries * 2;
 constexpr uint32_t kDevTagStep = 1u << 24;
 constexpr uint32_t kDevTagExt = 2u << 24;
 constexpr uint32_t kDevTagInit = 3u << 24;
+constexpr uint32_t kDevTagParticle = 4u << 24;
 constexpr int kExtWords = 24;        // extension words per thread held in shared memory
 
 // How a probability P/2^32 is drawn: never (P = 0), by table (0 < P < 2^32),
@@ -25,7 +26,10 @@ struct StepArgs {
   uint32_t flip;
   uint32_t omega_mode;   // kNever / kTable / kAlways for the thinning probability
   uint32_t rest_mode;    // same for the rest weight w_0
-  uint32_t general;      // 1: occupations so high that the fast path would mostly fail
+  uint32_t general;      // 1: skip the fast path (occupations so high that it would mostly
+                         //    fail, or the particle sampler)
+  uint32_t particle;     // 1: particle sampler (one word per particle, tag-4 stream); the
+                         //    table block then holds the boundaries B_0..B_Q (uint64)
   uint32_t key0, key1;   // Philox key = seed
   uint32_t replica;
   const uint32_t* tables;   // device, kDevBlockWords words (layout above)
@@ -272,6 +276,51 @@ __device__ __forceinline__ void collide_phased(const StepArgs& a, const uint32_t
     moving -= c;
     first = false;
   }
+}
+
+// The collision of one node with the particle sampler: particle k of velocity i
+// (in the order i = 0..Q-1, k = 0..m_i-1) takes word d of the tag-4 stream
+// (d counting all particles of the node) and stays when u < B_0, otherwise goes
+// to the velocity j with B_j <= u < B_{j+1}.  s holds B_0..B_Q as 64-bit integers
+// (B_Q = 2^32).  Counts of picked particles at or above each boundary give the
+// arrivals without a dynamically indexed array.
+template <int Q>
+__device__ void collide_particle(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
+                                 const uint32_t (&m)[Q], uint32_t (&out)[Q]) {
+  const unsigned long long* B = reinterpret_cast<const unsigned long long*>(s);
+  unsigned long long bound[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) bound[k] = B[k];
+  uint32_t ge[Q];  // ge[0]: picked particles; ge[k]: picked ones with u >= B_k
+#pragma unroll
+  for (int k = 0; k < Q; ++k) ge[k] = 0;
+  uint32_t d = 0;
+  uint4 blk = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    uint32_t picked = 0;
+    for (uint32_t k = 0; k < m[i]; ++k, ++d) {
+      if ((d & 3u) == 0) blk = philox_rk(make_uint4(node, t, a.replica, kDevTagParticle | (d >> 2)), a.rk);
+      const unsigned long long u = lane_of(blk, d & 3u);
+      if (u >= bound[0]) {
+        ++picked;
+#pragma unroll
+        for (int j = 1; j < Q; ++j) ge[j] += u >= bound[j] ? 1u : 0u;
+      }
+    }
+    out[i] = m[i] - picked;
+    ge[0] += picked;
+  }
+#pragma unroll
+  for (int j = 0; j < Q; ++j) out[j] += ge[j] - (j + 1 < Q ? ge[j + 1] : 0u);
+}
+
+// The general collision in whichever sampler the lattice uses.
+template <int Q, int K, int S>
+__device__ __forceinline__ void collide_general(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
+                                                const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
+  if (a.particle) collide_particle<Q>(a, s, node, t, m, out);
+  else collide_phased<Q, K, S>(a, s, node, t, m, out, xb);
 }
 
 // The collision of one node, fast path: every occupation <= 63, at most 63

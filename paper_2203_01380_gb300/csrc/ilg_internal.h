@@ -34,6 +34,8 @@ void build_alias_table(uint64_t P, AliasEntry* out);
 uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap);
 uint64_t quantise_probability(double p);
 uint32_t general_path(int Q, double omega_star, double mean_occupation);
+void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t* B);
+void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_rest, uint32_t* block);
 void weights(int lattice, double theta, double* w);
 
 // Poisson tables of the initial state, one per (velocity class, phase residue).

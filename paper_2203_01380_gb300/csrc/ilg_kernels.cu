@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) step_kernel(StepArgs a, const
       m[4] = a.flip ? n[3] : n[4];
     }
     if (a.general || !collide_try_fast<Q>(a, s, node, t, m, post)) {
-      collide_phased<Q, kExtWords, kStepThreads>(a, s, node, t, m, post, xb);
+      collide_general<Q, kExtWords, kStepThreads>(a, s, node, t, m, post, xb);
 #pragma unroll
       for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
     }

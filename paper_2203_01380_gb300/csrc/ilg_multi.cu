@@ -39,7 +39,7 @@ __device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s,
       m[4] = a.flip ? n[3] : n[4];
     }
     if (a.general || !collide_try_fast<Q>(a, s, uint32_t(at), t, m, post)) {
-      collide_phased<Q, kExtWords, kMultiThreads>(a, s, uint32_t(at), t, m, post, xb);
+      collide_general<Q, kExtWords, kMultiThreads>(a, s, uint32_t(at), t, m, post, xb);
 #pragma unroll
       for (int k = 0; k < Q; ++k) bad |= post[k] > 65535u;
     }
@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(kMultiThreads, 3) multi_step_kernel(MultiArgs 
     a.rest_mode = d.rest_mode;
     a.replica = d.replica;
     a.general = d.general;
+    a.particle = d.particle;
     const uint32_t t = d.t0 + sub;
     const bool odd = ((sub + d.phase) & 1u) != 0;
     const uint16_t* in = odd ? d.buf1 : d.buf0;

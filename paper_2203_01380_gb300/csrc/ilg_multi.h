@@ -20,7 +20,9 @@ struct LatDesc {
   uint32_t replica;
   uint32_t flip, omega_mode, rest_mode;
   uint32_t steps;       // sub-steps this lattice takes in the round (it idles after)
-  uint32_t general;     // 1: skip the fast path (high occupation)
+  uint32_t general;     // 1: skip the fast path (high occupation or particle sampler)
+  uint32_t particle;    // 1: particle sampler
+  uint32_t pad;
   uint16_t* buf0;
   uint16_t* buf1;
   const uint32_t* tables;  // kDevBlockWords words

@@ -44,7 +44,7 @@ struct Resident {
   size_t off_state = 0, state_bytes = 0;  // two buffers
   size_t off_tab = 0;
   uint32_t t = 0, remaining = 0, phase = 0;
-  uint32_t flip = 0, omega_mode = 0, rest_mode = 0, general = 0;
+  uint32_t flip = 0, omega_mode = 0, rest_mode = 0, general = 0, particle = 0;
   double t_admit = 0;
   int status = ILG_OK;
 };
@@ -190,13 +190,12 @@ bool admit(ilg_server* s, const Request& rq, Resident* out, cudaError_t* cerr, s
   const double omega_star = rq.p.omega_eff > 1.0 ? 2.0 - rq.p.omega_eff : rq.p.omega_eff;
   const uint64_t Po = quantise_probability(omega_star), Pr = quantise_probability(w[0]);
   r.flip = rq.p.omega_eff > 1.0 ? 1u : 0u;
-  r.general = general_path(5, omega_star, rq.p.n0);
+  r.particle = rq.p.sampler == ILG_SAMPLER_PARTICLE ? 1u : 0u;
+  r.general = general_path(5, omega_star, rq.p.n0) | r.particle;
   r.omega_mode = mode_of(Po);
   r.rest_mode = mode_of(Pr);
   std::vector<uint32_t> tables(kBlockWords, 0u);
-  AliasEntry* al = reinterpret_cast<AliasEntry*>(tables.data());
-  if (r.omega_mode == kTable) build_alias_table(Po, al);
-  if (r.rest_mode == kTable) build_alias_table(Pr, al + kAliasEntries);
+  build_table_block(5, rq.p.sampler, Po, Pr, tables.data());
   std::vector<uint32_t> init(init_words);
   std::copy(it.offset.begin(), it.offset.end(), init.begin());
   std::copy(it.count.begin(), it.count.end(), init.begin() + it.offset.size());
@@ -348,6 +347,7 @@ void worker_main(ilg_server* s) {
       d.rest_mode = r.rest_mode;
       d.steps = std::min(q, r.remaining);
       d.general = r.general;
+      d.particle = r.particle;
       d.buf0 = reinterpret_cast<uint16_t*>(s->d_arena + r.off_state);
       d.buf1 = reinterpret_cast<uint16_t*>(s->d_arena + r.off_state + r.state_bytes);
       d.tables = reinterpret_cast<const uint32_t*>(s->d_arena + r.off_tab);

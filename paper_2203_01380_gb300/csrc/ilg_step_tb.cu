@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kTbThreads, 2) step_tb_kernel(StepArgs a, cons
         m[3] = a.flip ? n[4] : n[3];
         m[4] = a.flip ? n[3] : n[4];
         if (a.general || !collide_try_fast<5>(a, tables, node, t0 + k, m, post)) {
-          collide_phased<5, kTbExtWords, kTbThreads>(a, tables, node, t0 + k, m, post, xbuf + threadIdx.x);
+          collide_general<5, kTbExtWords, kTbThreads>(a, tables, node, t0 + k, m, post, xbuf + threadIdx.x);
 #pragma unroll
           for (int i = 0; i < 5; ++i) bad |= post[i] > 65535u;
         }

@@ -3,6 +3,7 @@
 // Compiled with -ffp-contract=off: the Poisson tables and the initial means are
 // defined by a fixed sequence of IEEE double operations and libm calls, and must
 // come out the same on every host.
+#include <algorithm>
 #include "ilg_internal.h"
 
 #include <cmath>
@@ -106,6 +107,37 @@ uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap) {
 // node; with about omega* Q m removed on average (m = mean occupation per
 // velocity), above ~40 it would mostly fail and the general path is taken at once.
 // Either path gives the same result.
+// Particle sampler boundaries: B_0 = 2^32 - P_omega (below: the particle stays),
+// B_{j+1} = B_0 + floor(P_omega (P_rest (Q-1) + j (2^32 - P_rest)) / ((Q-1) 2^32))
+// for j = 0..Q-1, so a picked particle goes to rest with P_rest / 2^32 and to each
+// moving velocity with an equal share of the rest; B_Q = 2^32.
+void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t* B) {
+  typedef unsigned __int128 u128;
+  const u128 two32 = u128(1) << 32;
+  B[0] = uint64_t(two32 - P_omega);
+  const u128 den = u128(uint32_t(Q - 1)) << 32;
+  for (int j = 0; j < Q; ++j) {
+    const u128 num = u128(P_omega) * (u128(P_rest) * uint32_t(Q - 1) + u128(uint32_t(j)) * (two32 - P_rest));
+    B[j + 1] = B[0] + uint64_t(num / den);
+  }
+}
+
+// The device table block of a lattice: the two alias tables (binomial sampler) or
+// the particle boundaries.
+void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_rest, uint32_t* block) {
+  std::fill(block, block + kBlockWords, 0u);
+  if (sampler == ILG_SAMPLER_PARTICLE) {
+    uint64_t B[6] = {0, 0, 0, 0, 0, 0};
+    build_particle_bounds(Q, P_omega, P_rest, B);
+    std::memcpy(block, B, sizeof(B));
+    return;
+  }
+  const uint64_t two32 = uint64_t(1) << 32;
+  AliasEntry* al = reinterpret_cast<AliasEntry*>(block);
+  if (P_omega > 0 && P_omega < two32) build_alias_table(P_omega, al);
+  if (P_rest > 0 && P_rest < two32) build_alias_table(P_rest, al + kAliasEntries);
+}
+
 uint32_t general_path(int Q, double omega_star, double mean_occupation) {
   return omega_star * Q * mean_occupation > 40.0 ? 1u : 0u;
 }

@@ -45,7 +45,7 @@ def test_params_layout_matches_c(binding):
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ilg_params), offsetof(ilg_params, n0),
          offsetof(ilg_params, omega_eff), offsetof(ilg_params, seed), offsetof(ilg_params, replica),
-         offsetof(ilg_params, reserved));
+         offsetof(ilg_params, sampler));
   return 0;
 }
 """
@@ -57,7 +57,7 @@ int main(void) {
         got = [int(v) for v in subprocess.check_output([exe]).split()]
     P = binding.Params
     assert got == [ctypes.sizeof(P), P.n0.offset, P.omega_eff.offset, P.seed.offset, P.replica.offset,
-                   P.reserved.offset]
+                   P.sampler.offset]
 
 
 def test_binding_refuses_to_import_without_library(tmp_path):

@@ -46,6 +46,20 @@ def test_batch_init_and_run_match_oracle(B):
             assert np.array_equal(got, ref.run(ref.init(), 0, T)), (i, r)
 
 
+def test_batch_mixed_samplers_match_oracle(B):
+    """Rings with the particle sampler next to rings with the binomial sampler."""
+    reps = [dict(lattice=1, Lx=L, n0=n0, amp=0.0, omega_eff=w, seed=8, replica=i, sampler=i % 2)
+            for i, (L, n0, w) in enumerate([(40, 10.0, 1.5), (40, 10.0, 1.5), (130, 60.0, 0.7), (257, 25.0, 1.9),
+                                            (600, 5.0, 1.0), (64, 100.0, 1.2)])]
+    with B.Batch(reps) as bat:
+        bat.init()
+        bat.run(15)
+        for i, r in enumerate(reps):
+            got, t = bat.get_state(i)
+            ref = O.Lattice(**r)
+            assert t == 15 and np.array_equal(got, ref.run(ref.init(), 0, 15)), i
+
+
 def test_batch_equals_single_contexts(B):
     reps = mixed_replicas(seed=9)[:8]
     states = [inputs.random_state(3, 1, r["Lx"], r["n0"], seed=50 + i) for i, r in enumerate(reps)]

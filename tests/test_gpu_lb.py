@@ -146,13 +146,16 @@ def test_full_size_workload_y_invariant(B):
         assert np.abs(f[:, y, :] - ref[:, 0, :]).max() <= tol, y
 
 
-def test_gas_replica_mean_is_lattice_boltzmann(B):
-    """Sec. IV: the ensemble mean of the gas is the lattice Boltzmann solution.  From
-    a Poisson start the gas stays product-Poisson with means f, so the mean of R
-    replicas has variance f / R in every entry: chi-square over all entries."""
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_gas_replica_mean_is_lattice_boltzmann(B, sampler):
+    """Sec. IV: the ensemble mean of the gas (either sampler) is the lattice Boltzmann
+    solution.  From a Poisson start the gas stays product-Poisson with means f, so
+    the mean of R replicas has variance f / R in every entry: chi-square over all
+    entries."""
     stats = pytest.importorskip("scipy.stats")
     L, T, R = 96, 30, 400
-    base = dict(lattice=1, Lx=L, n0=20.0, amp=30.0, mode_mx=2, init_weighted=1, omega_eff=1.6, seed=23)
+    base = dict(lattice=1, Lx=L, n0=20.0, amp=30.0, mode_mx=2, init_weighted=1, omega_eff=1.6, seed=23,
+                sampler=sampler)
     reps = [dict(base, replica=r) for r in range(R)]
     with B.Batch(reps) as bat:
         bat.init()

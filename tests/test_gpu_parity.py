@@ -327,3 +327,41 @@ def test_set_state_high_mass_takes_general_path(B):
         lat.step(5)
         got, t = lat.get_state()
     assert t == 16 and np.array_equal(got, O.Lattice(**cfg).run(s_hi, 11, 5))
+
+
+# ---------------------------------------------------------------- particle sampler
+PARTICLE_CASES = [
+    # lattice, Lx, Ly, omega_eff, mean, hot
+    (1, 200, 1, 1.5, 20.0, 2),
+    (1, 64, 1, 0.6, 5.0, 0),
+    (2, 64, 24, 1.8, 10.0, 3),     # rows a multiple of 8: still the node-parallel kernel
+    (2, 37, 29, 1.0, 12.0, 0),     # omega* = 1: no particle stays
+    (2, 40, 16, 2.0, 9.0, 0),      # omega* = 0: every particle stays (pure flip)
+    (2, 33, 21, 0.3, 60.0, 2),
+]
+
+
+@pytest.mark.parametrize("lattice,Lx,Ly,omega,mean,hot", PARTICLE_CASES)
+def test_particle_sampler_bit_exact(B, lattice, Lx, Ly, omega, mean, hot):
+    Q = 3 if lattice == 1 else 5
+    s0 = inputs.random_state(Q, Ly, Lx, mean, seed=Lx + 3 * Ly, hot=hot, hot_value=700)
+    cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, omega_eff=omega, seed=41, replica=3, sampler=1)
+    got = gpu_run(B, cfg, 7, state=s0, t0=12)
+    assert np.array_equal(got, O.Lattice(**cfg).run(s0, 12, 7))
+
+
+def test_particle_sampler_init_and_temporal_blocking(B):
+    cfg = dict(lattice=2, Lx=50, Ly=44, n0=8.0, amp=6.0, mode_mx=1, omega_eff=1.4, seed=5, sampler=1)
+    ref = O.Lattice(**cfg)
+    with B.Lattice(**cfg) as lat:
+        lat.set_temporal_blocking(3)
+        lat.init()
+        lat.step(7)
+        got, t = lat.get_state()
+    assert t == 7 and np.array_equal(got, ref.run(ref.init(), 0, 7))
+
+
+def test_sampler_value_checked(B):
+    with pytest.raises(B.IlgError) as e:
+        B.Lattice(lattice=2, Lx=16, Ly=16, sampler=2)
+    assert e.value.status == B.ILG_E_INVALID

@@ -91,6 +91,20 @@ def test_small_request_matches_oracle(B):
     assert np.array_equal(res["state"], ref.run(ref.init(), 0, r["steps"]))
 
 
+def test_particle_sampler_requests_match_oracle(B):
+    """Requests with the particle sampler served beside binomial-sampler requests."""
+    base = dict(lattice=2, Lx=20, Ly=17, n0=9.0, amp=4.0, mode_mx=1, omega_eff=1.6, seed=SEED, steps=21)
+    reqs = [dict(base, replica=300 + i, sampler=i % 2) for i in range(4)]
+    with B.Server(SEED, 64 << 20, max_slots=4, quantum=8) as srv:
+        for i, r in enumerate(reqs):
+            srv.submit(i, want_state=True, **r)
+        srv.wait_idle(60)
+        res = {x["id"]: x for x in srv.poll()}
+    for i, r in enumerate(reqs):
+        ref = O.Lattice(**{k: v for k, v in r.items() if k != "steps"})
+        assert np.array_equal(res[i]["state"], ref.run(ref.init(), 0, r["steps"])), i
+
+
 def test_invalid_request_and_bounded_wait(B):
     with B.Server(SEED, 256 << 20, max_slots=4, quantum=4) as srv:
         with pytest.raises(B.IlgError):
