@@ -35,7 +35,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 NMAX = 64
 POISSON_KMAX = 4096
-D1Q3, D2Q5 = 1, 2
+D1Q3, D2Q5, D2Q9 = 1, 2, 3
 TWO32 = 1 << 32
 
 
@@ -58,6 +58,7 @@ class _StepParams(ctypes.Structure):
         ("thr_omega", ctypes.c_void_p), ("alias_omega", ctypes.c_void_p),
         ("thr_rest", ctypes.c_void_p), ("alias_rest", ctypes.c_void_p),
         ("sampler", ctypes.c_int32),
+        ("P_axis", ctypes.c_uint64), ("thr_axis", ctypes.c_void_p), ("alias_axis", ctypes.c_void_p),
     ]
 
 
@@ -106,7 +107,7 @@ def lib():
         L.oracle_collide_many.argtypes = [ctypes.POINTER(_StepParams), u32p, ctypes.c_uint32,
                                           ctypes.c_uint32, ctypes.c_uint32, u32p]
         L.oracle_collide_many.restype = None
-        L.oracle_particle_bounds.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
+        L.oracle_particle_bounds.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                              np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")]
         L.oracle_particle_bounds.restype = None
         _lib = L
@@ -118,7 +119,7 @@ def lib():
 # --------------------------------------------------------------------------
 
 def num_vel(lattice: int) -> int:
-    return 3 if lattice == D1Q3 else 5
+    return {D1Q3: 3, D2Q5: 5, D2Q9: 9}[lattice]
 
 
 def quantise(p: float) -> int:
@@ -131,7 +132,18 @@ def weights(lattice: int, theta: float):
     """w_i in storage order (rest first); theta = sum_i w_i v_{i,x}^2 per axis."""
     if lattice == D1Q3:
         return [1.0 - theta, theta / 2.0, theta / 2.0]
+    if lattice == D2Q9:
+        # products of the D1Q3 weights in x and y: rest, four axis, four diagonal
+        wa, wd = (theta * (1.0 - theta)) / 2.0, (theta * theta) / 4.0
+        return [(1.0 - theta) * (1.0 - theta)] + [wa] * 4 + [wd] * 4
     return [1.0 - 2.0 * theta, theta / 2.0, theta / 2.0, theta / 2.0, theta / 2.0]
+
+
+def axis_share(theta: float) -> float:
+    """D2Q9: probability that a moving particle takes an axis velocity,
+    4 w_axis / (1 - w_0), with the weights above."""
+    w = weights(D2Q9, theta)
+    return (4.0 * w[1]) / (1.0 - w[0])
 
 
 def split_omega(omega_eff: float):
@@ -168,10 +180,10 @@ def poisson_table(lam: float) -> np.ndarray:
     return T[:K].copy()
 
 
-def particle_bounds(lattice: int, P_omega: int, P_rest: int) -> list:
+def particle_bounds(lattice: int, P_omega: int, P_rest: int, P_axis: int = 0) -> list:
     """Boundaries B_0..B_Q of the particle sampler (one word per particle)."""
-    B = np.zeros(6, dtype=np.uint64)
-    lib().oracle_particle_bounds(lattice, P_omega, P_rest, B)
+    B = np.zeros(10, dtype=np.uint64)
+    lib().oracle_particle_bounds(lattice, P_omega, P_rest, P_axis, B)
     return [int(b) for b in B[:num_vel(lattice) + 1]]
 
 
@@ -186,7 +198,7 @@ class Lattice:
 
     def __init__(self, lattice, Lx, Ly=1, n0=10.0, amp=0.0, mode_mx=0, mode_my=0,
                  init_weighted=0, omega_eff=1.0, theta=1.0 / 3.0, seed=0, replica=0, sampler=0):
-        self.lattice, self.Lx, self.Ly = lattice, int(Lx), int(Ly if lattice == D2Q5 else 1)
+        self.lattice, self.Lx, self.Ly = lattice, int(Lx), int(Ly if lattice != D1Q3 else 1)
         self.sampler = int(sampler)   # 0: binomial draws through alias tables; 1: one word per particle
         self.n0, self.amp, self.mode_mx, self.mode_my = float(n0), float(amp), mode_mx, mode_my
         self.init_weighted, self.omega_eff, self.theta = init_weighted, float(omega_eff), float(theta)
@@ -199,11 +211,14 @@ class Lattice:
         none = (np.zeros(1, np.uint32), np.zeros(1, np.uint8))
         self._A_omega = alias_table(self.P_omega) if 0 < self.P_omega < TWO32 else none
         self._A_rest = alias_table(self.P_rest) if 0 < self.P_rest < TWO32 else none
+        self.P_axis = quantise(axis_share(self.theta)) if lattice == D2Q9 else 0
+        self._A_axis = alias_table(self.P_axis) if 0 < self.P_axis < TWO32 else none
 
     def _sp(self):
         return _StepParams(self.lattice, self.Lx, self.Ly, self.flip, self.P_omega, self.P_rest,
                            self.seed, self.replica, self._A_omega[0].ctypes.data, self._A_omega[1].ctypes.data,
-                           self._A_rest[0].ctypes.data, self._A_rest[1].ctypes.data, self.sampler)
+                           self._A_rest[0].ctypes.data, self._A_rest[1].ctypes.data, self.sampler,
+                           self.P_axis, self._A_axis[0].ctypes.data, self._A_axis[1].ctypes.data)
 
     def _ip(self):
         return _InitParams(self.lattice, self.Lx, self.Ly, self.n0, self.amp, self.mode_mx,
@@ -258,7 +273,7 @@ class Lattice:
         """State of the w x h window at (x0, y0) after t_end - t0 steps from the
         oracle's own initial state (light cone: a (w+2s) x (h+2s) patch)."""
         s = t_end - t0
-        pad_y = s if self.lattice == D2Q5 else 0
+        pad_y = s if self.lattice != D1Q3 else 0
         px, py = x0 - s, y0 - pad_y
         pw, ph = w + 2 * s, h + 2 * pad_y
         if initial is None:
@@ -266,8 +281,8 @@ class Lattice:
         else:
             patch = initial
         for k in range(s):
-            patch = self.step_region(patch, px + k, py + (k if self.lattice == D2Q5 else 0), t0 + k)
-            patch = patch[:, (1 if self.lattice == D2Q5 else 0):patch.shape[1] - (1 if self.lattice == D2Q5 else 0), 1:-1]
+            patch = self.step_region(patch, px + k, py + (k if self.lattice != D1Q3 else 0), t0 + k)
+            patch = patch[:, (1 if self.lattice != D1Q3 else 0):patch.shape[1] - (1 if self.lattice != D1Q3 else 0), 1:-1]
             patch = np.ascontiguousarray(patch)
         return patch
 

@@ -194,9 +194,12 @@ typedef struct {
   const uint32_t *thr_rest;  /* alias table of P_rest (unused if P_rest is 0 or 2^32) */
   const uint8_t *alias_rest;
   int32_t sampler;           /* 0: binomial draws (collide_node); 1: one word per particle */
+  uint64_t P_axis;           /* D2Q9: round(4 w_axis / (1 - w_0) * 2^32), share of the axis velocities */
+  const uint32_t *thr_axis;  /* alias table of P_axis (D2Q9 only) */
+  const uint8_t *alias_axis;
 } oracle_step_params;
 
-static int num_vel(int32_t lattice) { return lattice == 1 ? 3 : 5; }
+static int num_vel(int32_t lattice) { return lattice == 1 ? 3 : (lattice == 2 ? 5 : 9); }
 
 /* velocity sets, rest first: D1Q3 {0, +1, -1}; D2Q5 {0, +x, -x, +y, -y} */
 static const int VX3[3] = {0, 1, -1};
@@ -204,6 +207,10 @@ static const int VX5[5] = {0, 1, -1, 0, 0};
 static const int VY5[5] = {0, 0, 0, 1, -1};
 static const int OPP3[3] = {0, 2, 1};
 static const int OPP5[5] = {0, 2, 1, 4, 3};
+/* D2Q9: rest, +x, -x, +y, -y, (+1,+1), (-1,-1), (+1,-1), (-1,+1) */
+static const int VX9[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+static const int VY9[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+static const int OPP9[9] = {0, 2, 1, 4, 3, 6, 5, 8, 7};
 
 /* sequential reader of the extension stream of one node and step */
 typedef struct {
@@ -246,8 +253,8 @@ static uint32_t popcount32(uint32_t v) {
 static void collide_node(const oracle_step_params *p, uint32_t node, uint32_t t,
                          const uint32_t *m, uint32_t *out) {
   int Q = num_vel(p->lattice);
-  uint32_t W[8];
-  for (uint32_t d = 0; d < 8; ++d) W[d] = stream_word(p->seed, node, t, p->replica, OR_TAG_STEP, d);
+  uint32_t W[16];
+  for (uint32_t d = 0; d < 16; ++d) W[d] = stream_word(p->seed, node, t, p->replica, OR_TAG_STEP, d);
   ext_reader ext = {p, node, t, 0};
 
   /* thinning: r_i = Binomial(m_i, omega*), slot word i */
@@ -261,6 +268,45 @@ static void collide_node(const oracle_step_params *p, uint32_t node, uint32_t t,
   uint32_t to_rest = binomial_chunked(p->P_rest, p->thr_rest, p->alias_rest, removed_total, W[Q], &ext);
   out[0] += to_rest;
   uint32_t moving = removed_total - to_rest;
+
+  if (Q == 9) {
+    /* D2Q9: the moving particles split into axis and diagonal ones, R_a =
+     * Binomial(moving, 4 w_axis / (1 - w_0)) with slot word 10; then per group of 32
+     * axis particles an axis word A and a sign word B (slot words 11, 12 for the
+     * first group) as on D2Q5, and per group of 32 diagonal particles an x-sign word
+     * X and a y-sign word Y (slot words 13, 14 for the first group): (0,0) -> (+1,+1),
+     * (1,1) -> (-1,-1), (0,1) -> (+1,-1), (1,0) -> (-1,+1).  Later groups take
+     * extension words, two per group, axis groups before diagonal groups. */
+    uint32_t axis = binomial_chunked(p->P_axis, p->thr_axis, p->alias_axis, moving, W[10], &ext);
+    uint32_t diag = moving - axis;
+    uint32_t group = 0;
+    while (axis > 0) {
+      uint32_t c = axis < 32 ? axis : 32;
+      uint32_t mask = c == 32 ? 0xFFFFFFFFu : ((1u << c) - 1u);
+      uint32_t a = group == 0 ? W[11] : ext_next(&ext);
+      uint32_t b = group == 0 ? W[12] : ext_next(&ext);
+      out[1] += popcount32(~a & ~b & mask);
+      out[2] += popcount32(~a & b & mask);
+      out[3] += popcount32(a & ~b & mask);
+      out[4] += popcount32(a & b & mask);
+      axis -= c;
+      group += 1;
+    }
+    group = 0;
+    while (diag > 0) {
+      uint32_t c = diag < 32 ? diag : 32;
+      uint32_t mask = c == 32 ? 0xFFFFFFFFu : ((1u << c) - 1u);
+      uint32_t x = group == 0 ? W[13] : ext_next(&ext);
+      uint32_t y = group == 0 ? W[14] : ext_next(&ext);
+      out[5] += popcount32(~x & ~y & mask);
+      out[6] += popcount32(x & y & mask);
+      out[7] += popcount32(~x & y & mask);
+      out[8] += popcount32(x & ~y & mask);
+      diag -= c;
+      group += 1;
+    }
+    return;
+  }
 
   /* uniform choice among the moving velocities, groups of 32 particles */
   uint32_t group = 0;
@@ -302,9 +348,22 @@ static void collide_node(const oracle_step_params *p, uint32_t node, uint32_t t,
  * and each moving velocity with an equal share of the remainder (to within one
  * unit of 2^-32 per boundary).
  */
-static void particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t *B) {
+static void particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis, uint64_t *B) {
   const unsigned __int128 two32 = (unsigned __int128)1 << 32;
   B[0] = (uint64_t)(two32 - P_omega);
+  if (Q == 9) {
+    /* shares of a picked particle, in units of 1 / (4 2^64): rest 4 P_rest 2^32, each axis
+     * velocity (2^32 - P_rest) P_axis, each diagonal (2^32 - P_rest) (2^32 - P_axis) */
+    unsigned __int128 cum = (unsigned __int128)4 * P_rest * two32;
+    const unsigned __int128 den = (unsigned __int128)4 << 64;
+    for (int j = 0; j < 9; ++j) {
+      if (j >= 1 && j <= 4) cum += (two32 - P_rest) * (unsigned __int128)P_axis;
+      if (j >= 5) cum += (two32 - P_rest) * (two32 - P_axis);
+      /* P_omega * cum <= 2^32 * 2^66 fits in 128 bits */
+      B[j + 1] = B[0] + (uint64_t)(((unsigned __int128)P_omega * cum) / den);
+    }
+    return;
+  }
   for (int j = 0; j < Q; ++j) {
     unsigned __int128 num = (unsigned __int128)P_omega *
                             ((unsigned __int128)P_rest * (unsigned)(Q - 1) + (unsigned __int128)j * (two32 - P_rest));
@@ -316,8 +375,8 @@ static void particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t *
 static void collide_node_particle(const oracle_step_params *p, uint32_t node, uint32_t t,
                                   const uint32_t *m, uint32_t *out) {
   int Q = num_vel(p->lattice);
-  uint64_t B[6];
-  particle_bounds(Q, p->P_omega, p->P_rest, B);
+  uint64_t B[10];
+  particle_bounds(Q, p->P_omega, p->P_rest, p->P_axis, B);
   for (int i = 0; i < Q; ++i) out[i] = 0;
   uint32_t d = 0;
   for (int i = 0; i < Q; ++i) {
@@ -342,8 +401,8 @@ static void collide_any(const oracle_step_params *p, uint32_t node, uint32_t t, 
 }
 
 /* exported for the tests: the boundaries B_0..B_Q */
-void oracle_particle_bounds(int32_t lattice, uint64_t P_omega, uint64_t P_rest, uint64_t *B) {
-  particle_bounds(num_vel(lattice), P_omega, P_rest, B);
+void oracle_particle_bounds(int32_t lattice, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis, uint64_t *B) {
+  particle_bounds(num_vel(lattice), P_omega, P_rest, P_axis, B);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -363,22 +422,23 @@ int oracle_step_region(const oracle_step_params *p, const uint16_t *in, uint16_t
                        uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, int periodic,
                        uint32_t t) {
   int Q = num_vel(p->lattice);
-  const int *VX = Q == 3 ? VX3 : VX5;
-  const int *OPP = Q == 3 ? OPP3 : OPP5;
+  const int *VX = Q == 3 ? VX3 : (Q == 5 ? VX5 : VX9);
+  const int *VY = Q == 3 ? VX3 : (Q == 5 ? VY5 : VY9); /* unused for D1Q3 */
+  const int *OPP = Q == 3 ? OPP3 : (Q == 5 ? OPP5 : OPP9);
   size_t plane = (size_t)w * h;
   memset(out, 0, sizeof(uint16_t) * plane * Q);
   for (uint32_t j = 0; j < h; ++j) {
     for (uint32_t i = 0; i < w; ++i) {
       uint32_t gx = (x0 + i) % p->Lx, gy = (y0 + j) % p->Ly;
       uint32_t node = gx + p->Lx * gy;
-      uint32_t n[5], m[5], post[5];
+      uint32_t n[9], m[9], post[9];
       for (int v = 0; v < Q; ++v) n[v] = in[v * plane + (size_t)j * w + i];
       for (int v = 0; v < Q; ++v) m[v] = p->flip ? n[OPP[v]] : n[v];
       collide_any(p, node, t, m, post);
       for (int v = 0; v < Q; ++v) {
         if (post[v] > 65535u) return 3;
         long di = (long)i + VX[v];
-        long dj = (long)j + (Q == 5 ? VY5[v] : 0);
+        long dj = (long)j + (Q == 3 ? 0 : VY[v]);
         if (periodic) {
           di = (di + (long)w) % (long)w;
           dj = (dj + (long)h) % (long)h;
@@ -446,7 +506,9 @@ double oracle_init_lambda(const oracle_init_params *p, uint32_t gx, uint32_t gy,
   if (p->init_weighted) {
     double w;
     if (Q == 3) w = v == 0 ? 1.0 - p->theta : p->theta / 2.0;
-    else w = v == 0 ? 1.0 - 2.0 * p->theta : p->theta / 2.0;
+    else if (Q == 5) w = v == 0 ? 1.0 - 2.0 * p->theta : p->theta / 2.0;
+    else w = v == 0 ? (1.0 - p->theta) * (1.0 - p->theta)
+                    : (v <= 4 ? (p->theta * (1.0 - p->theta)) / 2.0 : (p->theta * p->theta) / 4.0);
     return w * ((double)Q * p->n0 + p->amp * s);
   }
   return p->n0 + (p->amp * s) / (double)Q;

@@ -20,7 +20,10 @@ D1Q3 uses the transform matrix the paper prints (Sec. IV, Eq. transform), rows
 (rho, j, Pi) over velocities (-1, 0, +1), reordered here to the storage order
 (0, +1, -1).  D2Q5 (not in the paper) uses the analogous Hermite basis: 1,
 v_x / sqrt(theta), v_y / sqrt(theta), (v^2 - 2 theta) / sqrt(2 theta (1 - 2 theta)),
-(v_x^2 - v_y^2) / sqrt(2 theta), the last two relaxing with omega.
+(v_x^2 - v_y^2) / sqrt(2 theta), the last two relaxing with omega.  D2Q9 (weights the
+products of the D1Q3 weights in x and y) uses the products e_a(v_x) e_b(v_y) of the
+paper's D1Q3 rows e_0 = 1, e_1 = v / sqrt(theta), e_2 = (v^2 - theta) / sqrt(theta (1 -
+theta)); a product is odd in the velocity when a + b is odd.
 
 Everything is plain numpy in double precision, one full matrix product per node,
 no fusion.  Pins: ``tests/test_oracle_lb.py``.
@@ -31,10 +34,11 @@ import math
 
 import numpy as np
 
-from . import D1Q3, D2Q5, Lattice, weights
+from . import D1Q3, D2Q5, D2Q9, Lattice, weights
 
 # velocities in storage order (rest first); D2Q5 rows are (v_x, v_y)
-_VEL = {D1Q3: np.array([[0], [1], [-1]]), D2Q5: np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [0, -1]])}
+_VEL = {D1Q3: np.array([[0], [1], [-1]]), D2Q5: np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [0, -1]]),
+        D2Q9: np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [0, -1], [1, 1], [-1, -1], [1, -1], [-1, 1]])}
 
 
 def velocities(lattice: int) -> np.ndarray:
@@ -53,6 +57,16 @@ def basis(lattice: int, theta: float):
                           [p, -q, p]])
         # storage order (0, +1, -1) = paper columns (1, 2, 0)
         return paper[:, [1, 2, 0]], np.array([False, True, False])
+    if lattice == D2Q9:
+        v = _VEL[D2Q9].astype(float)
+        def e(a, u):
+            return [np.ones_like(u), u / math.sqrt(theta), (u * u - theta) / math.sqrt(theta * (1.0 - theta))][a]
+        rows, odd = [], []
+        for a in range(3):
+            for b in range(3):
+                rows.append(e(a, v[:, 0]) * e(b, v[:, 1]))
+                odd.append((a + b) % 2 == 1)
+        return np.array(rows), np.array(odd)
     v = _VEL[D2Q5].astype(float)
     vx, vy = v[:, 0], v[:, 1]
     v2 = vx * vx + vy * vy
@@ -76,9 +90,9 @@ class LB:
     """One periodic lattice of the MRT scheme; state f[i, y, x] (float64)."""
 
     def __init__(self, lattice, Lx, Ly=1, theta=1.0 / 3.0, omega_j=1.0, omega=1.0):
-        self.lattice, self.Lx, self.Ly = lattice, int(Lx), int(Ly if lattice == D2Q5 else 1)
+        self.lattice, self.Lx, self.Ly = lattice, int(Lx), int(Ly if lattice != D1Q3 else 1)
         self.theta, self.omega_j, self.omega = float(theta), float(omega_j), float(omega)
-        self.Q = 3 if lattice == D1Q3 else 5
+        self.Q = {D1Q3: 3, D2Q5: 5, D2Q9: 9}[lattice]
         self.w = np.array(weights(lattice, self.theta))
         self.m, self.odd = basis(lattice, self.theta)
         # relaxation factor (1 - omega^a) per moment; omega^rho = 1
@@ -114,7 +128,7 @@ class LB:
         out = np.empty_like(post)
         for i in range(self.Q):
             vx = int(self.v[i, 0])
-            vy = int(self.v[i, 1]) if self.lattice == D2Q5 else 0
+            vy = int(self.v[i, 1]) if self.lattice != D1Q3 else 0
             out[i] = np.roll(np.roll(post[i], vx, axis=1), vy, axis=0)
         return out
 

@@ -31,7 +31,11 @@ def transition(lat: O.Lattice):
     Q = lat.Q
     om = Fraction(lat.P_omega, 1 << 32)
     w0 = Fraction(lat.P_rest, 1 << 32)
-    w = [w0] + [(1 - w0) / (Q - 1)] * (Q - 1)
+    if Q == 9:
+        pa = Fraction(lat.P_axis, 1 << 32)
+        w = [w0] + [(1 - w0) * pa / 4] * 4 + [(1 - w0) * (1 - pa) / 4] * 4
+    else:
+        w = [w0] + [(1 - w0) / (Q - 1)] * (Q - 1)
     return [[(1 - om) * (1 if i == j else 0) + om * w[j] for j in range(Q)] for i in range(Q)]
 
 
@@ -89,6 +93,9 @@ CASES = [
     (O.D2Q5, (0, 0, 1, 1, 1), 1.0, 1.0 / 3.0),
     (O.D2Q5, (2, 1, 1, 1, 1), 0.6, 0.4),
     (O.D2Q5, (0, 3, 0, 0, 2), 0.05, 1.0 / 3.0),
+    (O.D2Q9, (1, 1, 0, 0, 0, 1, 0, 0, 1), 0.5, 1.0 / 3.0),
+    (O.D2Q9, (0, 0, 0, 0, 0, 2, 0, 0, 0), 1.0, 1.0 / 3.0),
+    (O.D2Q9, (2, 0, 1, 0, 0, 0, 0, 1, 0), 0.7, 0.45),
 ]
 
 
@@ -103,6 +110,8 @@ def test_collision_law_exact(lattice, m, omega, theta):
 
 
 @pytest.mark.parametrize("lattice,m,omega", [
+    (O.D2Q9, (120, 70, 0, 45, 200, 5, 66, 90, 1), 0.6),
+    (O.D2Q9, (20, 20, 20, 20, 20, 20, 20, 20, 20), 1.0),
     (O.D2Q5, (300, 70, 0, 45, 200), 0.5),
     (O.D2Q5, (40, 40, 40, 40, 40), 0.9),
     (O.D1Q3, (150, 260, 90), 0.8),
@@ -179,10 +188,11 @@ def test_paper_transform_is_hermite_orthogonal_with_weights():
 # quantisation, so it is compared with the same exact enumeration.
 
 @pytest.mark.parametrize("lattice,omega,theta", [(O.D1Q3, 0.3, 1 / 3), (O.D1Q3, 1.0, 0.6), (O.D2Q5, 0.45, 1 / 3),
-                                                 (O.D2Q5, 0.0, 0.4), (O.D2Q5, 1.0, 0.2)])
+                                                 (O.D2Q5, 0.0, 0.4), (O.D2Q5, 1.0, 0.2), (O.D2Q9, 0.3, 1 / 3),
+                                                 (O.D2Q9, 1.0, 0.6)])
 def test_particle_bounds_realise_the_law(lattice, omega, theta):
     lat = O.Lattice(lattice, 8, 8, omega_eff=omega, theta=theta)
-    B = O.particle_bounds(lattice, lat.P_omega, lat.P_rest)
+    B = O.particle_bounds(lattice, lat.P_omega, lat.P_rest, lat.P_axis)
     Q = lat.Q
     assert len(B) == Q + 1 and B[-1] == 1 << 32
     assert all(B[k] <= B[k + 1] for k in range(Q))
@@ -202,7 +212,8 @@ def test_particle_sampler_law_exact(lattice, m, omega, theta):
     assert chi2_pvalue(out, law) > 1e-4
 
 
-@pytest.mark.parametrize("lattice,m,omega", [(O.D2Q5, (300, 70, 0, 45, 200), 0.5), (O.D1Q3, (150, 260, 90), 0.8)])
+@pytest.mark.parametrize("lattice,m,omega", [(O.D2Q5, (300, 70, 0, 45, 200), 0.5), (O.D1Q3, (150, 260, 90), 0.8),
+                                             (O.D2Q9, (30, 70, 0, 45, 20, 5, 66, 90, 1), 0.6)])
 def test_particle_sampler_moments_large(lattice, m, omega):
     lat = O.Lattice(lattice, 16, 16, omega_eff=omega, seed=6, sampler=1)
     P = np.array([[float(v) for v in row] for row in transition(lat)])

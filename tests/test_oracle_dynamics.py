@@ -22,7 +22,7 @@ import oracle as O
 from paper_2203_01380_gb300 import inputs
 
 
-@pytest.mark.parametrize("lattice,Lx,Ly", [(O.D1Q3, 37, 1), (O.D2Q5, 19, 13)])
+@pytest.mark.parametrize("lattice,Lx,Ly", [(O.D1Q3, 37, 1), (O.D2Q5, 19, 13), (O.D2Q9, 11, 9)])
 def test_pure_flip_has_period_two(lattice, Lx, Ly):
     lat = O.Lattice(lattice, Lx, Ly, omega_eff=2.0, seed=7)
     assert lat.flip == 1 and lat.P_omega == 0
@@ -34,7 +34,8 @@ def test_pure_flip_has_period_two(lattice, Lx, Ly):
     assert np.array_equal(lat.run(s0, 10, 8), s0)
 
 
-@pytest.mark.parametrize("lattice,omega", [(O.D1Q3, 0.7), (O.D1Q3, 1.9), (O.D2Q5, 1.0), (O.D2Q5, 1.3)])
+@pytest.mark.parametrize("lattice,omega", [(O.D1Q3, 0.7), (O.D1Q3, 1.9), (O.D2Q5, 1.0), (O.D2Q5, 1.3),
+                                          (O.D2Q9, 0.8), (O.D2Q9, 1.6)])
 def test_mass_conserved_every_step(lattice, omega):
     lat = O.Lattice(lattice, 33, 17, omega_eff=omega, seed=9)
     s = inputs.random_state(lat.Q, lat.Ly, lat.Lx, 20.0, seed=2, hot=5, hot_value=700)
@@ -115,7 +116,7 @@ def test_equilibrium_is_product_poisson():
     assert abs(Sk.mean() / rho - 1) < 0.08
 
 
-@pytest.mark.parametrize("lattice,Lx,Ly", [(O.D1Q3, 23, 1), (O.D2Q5, 11, 7)])
+@pytest.mark.parametrize("lattice,Lx,Ly", [(O.D1Q3, 23, 1), (O.D2Q5, 11, 7), (O.D2Q9, 10, 7)])
 def test_free_streaming_direction(lattice, Lx, Ly):
     """With omega_eff so small that omega* quantises to 0 (and no flip) the step is
     streaming alone, n_i(x + v_i, t + 1) = n_i(x, t) (Sec. II, Eq. ilgeq), with
@@ -124,6 +125,8 @@ def test_free_streaming_direction(lattice, Lx, Ly):
     assert lat.P_omega == 0 and lat.flip == 0
     s = inputs.random_state(lat.Q, lat.Ly, lat.Lx, 9.0, seed=4)
     out = lat.step(s, 0)
-    shifts = [(0, 0), (0, 1), (0, -1)] if lattice == O.D1Q3 else [(0, 0), (0, 1), (0, -1), (1, 0), (-1, 0)]
+    shifts = {O.D1Q3: [(0, 0), (0, 1), (0, -1)],
+              O.D2Q5: [(0, 0), (0, 1), (0, -1), (1, 0), (-1, 0)],
+              O.D2Q9: [(0, 0), (0, 1), (0, -1), (1, 0), (-1, 0), (1, 1), (-1, -1), (-1, 1), (1, -1)]}[lattice]
     for v, (dy, dx) in enumerate(shifts):
         assert np.array_equal(out[v], np.roll(np.roll(s[v], dy, axis=0), dx, axis=1)), v

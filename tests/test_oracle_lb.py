@@ -24,7 +24,8 @@ import oracle as O
 from oracle import lb as L
 
 
-@pytest.mark.parametrize("lattice,theta", [(O.D1Q3, 1 / 3), (O.D1Q3, 0.45), (O.D2Q5, 1 / 3), (O.D2Q5, 0.2)])
+@pytest.mark.parametrize("lattice,theta", [(O.D1Q3, 1 / 3), (O.D1Q3, 0.45), (O.D2Q5, 1 / 3), (O.D2Q5, 0.2),
+                                           (O.D2Q9, 1 / 3), (O.D2Q9, 0.6)])
 def test_basis_orthonormal_both_ways(lattice, theta):
     m, odd = L.basis(lattice, theta)
     w = np.array(O.weights(lattice, theta))
@@ -32,14 +33,15 @@ def test_basis_orthonormal_both_ways(lattice, theta):
     assert np.allclose(m @ np.diag(w) @ m.T, np.eye(Q), atol=1e-14)
     assert np.allclose(m.T @ m * w[None, :], np.eye(Q), atol=1e-14)
     v = L.velocities(lattice)
-    opp = [0, 2, 1] if lattice == O.D1Q3 else [0, 2, 1, 4, 3]
+    opp = {O.D1Q3: [0, 2, 1], O.D2Q5: [0, 2, 1, 4, 3], O.D2Q9: [0, 2, 1, 4, 3, 6, 5, 8, 7]}[lattice]
     for a in range(Q):   # odd moments change sign under v -> -v, even ones do not
         assert np.allclose(m[a, opp], -m[a] if odd[a] else m[a])
-    assert odd.sum() == v.shape[1]
+    assert odd.sum() == {O.D1Q3: 1, O.D2Q5: 2, O.D2Q9: 4}[lattice]
 
 
 @pytest.mark.parametrize("lattice,omega_j,omega", [(O.D1Q3, 1.6, 0.4), (O.D1Q3, 0.3, 1.7),
-                                                   (O.D2Q5, 1.9, 0.1), (O.D2Q5, 0.8, 1.2)])
+                                                   (O.D2Q5, 1.9, 0.1), (O.D2Q5, 0.8, 1.2),
+                                                   (O.D2Q9, 1.7, 0.5), (O.D2Q9, 0.4, 1.3)])
 def test_moment_space_collision(lattice, omega_j, omega):
     theta = 0.3
     lb = L.LB(lattice, 5, 4, theta=theta, omega_j=omega_j, omega=omega)
@@ -55,28 +57,31 @@ def test_moment_space_collision(lattice, omega_j, omega):
         assert np.allclose(np.einsum("i,iyx->yx", v[:, d], g), (1 - omega_j) * j, atol=1e-12)
     # second moments about their equilibrium values
     seconds = [vv - v.shape[1] * theta]
-    if lattice == O.D2Q5:
+    if lattice != O.D1Q3:
         seconds.append(v[:, 0] ** 2 - v[:, 1] ** 2)
+    if lattice == O.D2Q9:
+        seconds.append(v[:, 0] * v[:, 1])
     for s in seconds:
         pi = np.einsum("i,iyx->yx", s, f)
         assert np.allclose(np.einsum("i,iyx->yx", s, g), (1 - omega) * pi, atol=1e-11)
 
 
-@pytest.mark.parametrize("lattice,omega_eff", [(O.D1Q3, 1.5), (O.D1Q3, 0.6), (O.D2Q5, 1.8), (O.D2Q5, 1.0)])
+@pytest.mark.parametrize("lattice,omega_eff", [(O.D1Q3, 1.5), (O.D1Q3, 0.6), (O.D2Q5, 1.8), (O.D2Q5, 1.0),
+                                               (O.D2Q9, 1.4), (O.D2Q9, 0.7)])
 def test_collision_is_flip_plus_relaxation(lattice, omega_eff):
     oj, om = L.rates_from_omega_eff(omega_eff)
     lb = L.LB(lattice, 6, 3, omega_j=oj, omega=om)
     rng = np.random.default_rng(5)
     f = rng.uniform(0.0, 50.0, size=lb.shape)
     flip, ostar = O.split_omega(omega_eff)
-    opp = [0, 2, 1] if lattice == O.D1Q3 else [0, 2, 1, 4, 3]
+    opp = {O.D1Q3: [0, 2, 1], O.D2Q5: [0, 2, 1, 4, 3], O.D2Q9: [0, 2, 1, 4, 3, 6, 5, 8, 7]}[lattice]
     F = f[opp] if flip else f
     w = np.array(O.weights(lattice, 1 / 3))
     expect = F + ostar * (w[:, None, None] * F.sum(0)[None] - F)
     assert np.allclose(lb.collide(f), expect, rtol=1e-13, atol=1e-12)
 
 
-@pytest.mark.parametrize("lattice,Lx,Ly", [(O.D1Q3, 23, 1), (O.D2Q5, 11, 9)])
+@pytest.mark.parametrize("lattice,Lx,Ly", [(O.D1Q3, 23, 1), (O.D2Q5, 11, 9), (O.D2Q9, 9, 8)])
 def test_full_relaxation_is_random_walk(lattice, Lx, Ly):
     lb = L.LB(lattice, Lx, Ly, theta=0.3, omega_j=1.0, omega=1.0)
     rng = np.random.default_rng(8)
@@ -90,13 +95,13 @@ def test_full_relaxation_is_random_walk(lattice, Lx, Ly):
         for y in range(lb.Ly):          # brute-force convolution with the weights
             for x in range(lb.Lx):
                 for i in range(lb.Q):
-                    dy = int(v[i, 1]) if lattice == O.D2Q5 else 0
+                    dy = int(v[i, 1]) if lattice != O.D1Q3 else 0
                     nxt[(y + dy) % lb.Ly, (x + int(v[i, 0])) % lb.Lx] += w[i] * rho[y, x]
         rho = nxt
         assert np.allclose(f.sum(0), rho, rtol=1e-13)
 
 
-@pytest.mark.parametrize("lattice", [O.D1Q3, O.D2Q5])
+@pytest.mark.parametrize("lattice", [O.D1Q3, O.D2Q5, O.D2Q9])
 def test_streaming_and_period_two(lattice):
     lb0 = L.LB(lattice, 13, 7, omega_j=0.0, omega=0.0)
     rng = np.random.default_rng(9)
@@ -104,7 +109,7 @@ def test_streaming_and_period_two(lattice):
     g = lb0.run(f, 5)
     v = L.velocities(lattice)
     for i in range(lb0.Q):
-        dy = int(v[i, 1]) if lattice == O.D2Q5 else 0
+        dy = int(v[i, 1]) if lattice != O.D1Q3 else 0
         assert np.allclose(g[i], np.roll(np.roll(f[i], 5 * int(v[i, 0]), axis=1), 5 * dy, axis=0), rtol=1e-13)
     lb2 = L.LB(lattice, 13, 7, omega_j=2.0, omega=0.0)
     f1 = lb2.step(f)
@@ -112,7 +117,8 @@ def test_streaming_and_period_two(lattice):
     assert np.allclose(lb2.step(f1), f, rtol=1e-14)
 
 
-@pytest.mark.parametrize("lattice,omega_eff", [(O.D1Q3, 1.5), (O.D1Q3, 0.8), (O.D1Q3, 1.9), (O.D2Q5, 1.3)])
+@pytest.mark.parametrize("lattice,omega_eff", [(O.D1Q3, 1.5), (O.D1Q3, 0.8), (O.D1Q3, 1.9), (O.D2Q5, 1.3),
+                                               (O.D2Q9, 1.6)])
 def test_mass_conserved(lattice, omega_eff):
     oj, om = L.rates_from_omega_eff(omega_eff)
     lb = L.LB(lattice, 29, 8, omega_j=oj, omega=om)
@@ -202,3 +208,23 @@ def test_ensemble_prediction_against_gas_replicas():
         assert abs(cov[t].imag - pred["cov_im"][t]) < 6 * se, t
     # the correlation must actually decay (omega^j = 1.7: D > 0)
     assert pred["cov_re"][T] < 0.97 * pred["cov_re"][0]
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_d2q9_gas_mean_is_lattice_boltzmann(sampler):
+    """D2Q9: replica mean of the integer oracle against the lattice Boltzmann state."""
+    stats = pytest.importorskip("scipy.stats")
+    cfg = dict(n0=8.0, amp=20.0, mode_mx=1, init_weighted=1, omega_eff=1.5, seed=19, sampler=sampler)
+    Lx, Ly, T, R = 6, 5, 4, 300
+    oj, om = L.rates_from_omega_eff(cfg["omega_eff"])
+    lb = L.LB(O.D2Q9, Lx, Ly, omega_j=oj, omega=om)
+    f = lb.run(lb.init_mean(n0=8.0, amp=20.0, mode_mx=1, init_weighted=1), T)
+    lat = O.Lattice(O.D2Q9, Lx, Ly, **cfg)
+    acc = np.zeros(lb.shape)
+    for r in range(R):
+        lat.replica = r
+        acc += lat.run(lat.init(), 0, T)
+    mean = acc / R
+    chi2 = float((((mean - f) ** 2) / (f / R)).sum())
+    dof = f.size
+    assert stats.chi2.ppf(1e-6, dof) < chi2 < stats.chi2.ppf(1 - 1e-6, dof), chi2
