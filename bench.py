@@ -293,6 +293,33 @@ def measure_particle(torch, B, dev, side):
             "kernel": "step_kernel<5> (general path, one Philox word per particle)"}
 
 
+def measure_d2q9(torch, B, dev, side):
+    """The D2Q9 lattice (9 velocities, product weights) on the main workload's size."""
+    cfg = {k: v for k, v in inputs.LARGE_D2Q9.items() if k != "steps"}
+    cfg.update(Lx=side, Ly=side)
+    st = torch.cuda.Stream(dev)
+    T = 20
+    with B.Lattice(**cfg, stream=st) as lat:
+        lat.init()
+        lat.step(2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        lat.step(T)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / T
+    nodes = side * side
+    pk = peaks()
+    hpk = pk["hbm_gbs"] if pk else 6800.0
+    gbs = 36 * nodes / (ms / 1e3) / 1e9
+    return {"workload": f"large_d2q9: D2Q9 {side}x{side}, Poisson mean 10 per velocity, omega_eff 1.8, {T} steps",
+            "value": nodes / (ms / 1e3) / 1e9, "unit": "GNUPS", "ms_per_step": ms,
+            "hbm": {"achieved": gbs, "peak": hpk, "unit": "GB/s", "frac": gbs / hpk,
+                    "bytes_per_node_update": 36},
+            "kernel": "step9_kernel (node-parallel, four Philox blocks per node)"}
+
+
 def serve_stream(B, reqs, slots, smallest_first):
     """Submit requests at their arrival times; returns results, wall time, stats."""
     with B.Server(5, 48 << 30, max_slots=slots, quantum=32) as srv:
@@ -392,7 +419,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip every measurement beyond the main workload")
-    ap.add_argument("--extra", default="tb,batched,lb,ensemble,particle,serving",
+    ap.add_argument("--extra", default="tb,batched,lb,ensemble,particle,d2q9,serving",
                     help="comma-separated measurements beyond the main workload")
     ap.add_argument("--lb-side", type=int, default=0, help="side of the lattice Boltzmann workload (default 16384)")
     args = ap.parse_args()
@@ -504,6 +531,8 @@ def main():
             extra["ensemble"] = measure_ensemble(torch, B, dev)
         if "particle" in parts:
             extra["particle_sampler"] = measure_particle(torch, B, dev, args.side)
+        if "d2q9" in parts:
+            extra["d2q9"] = measure_d2q9(torch, B, dev, args.side)
         if "serving" in parts:
             extra["serving"] = measure_serving(B)
 

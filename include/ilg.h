@@ -13,7 +13,8 @@
  *
  * Conventions
  *   - Occupations are uint16, stored as Q planes n[i][y][x] (x fastest), velocity
- *     order rest first: D1Q3 (0, +1, -1); D2Q5 (0, +x, -x, +y, -y), y = row.
+ *     order rest first: D1Q3 (0, +1, -1); D2Q5 (0, +x, -x, +y, -y), y = row;
+ *     D2Q9 (0, +x, -x, +y, -y, (+1,+1), (-1,-1), (+1,-1), (-1,+1)).
  *   - The library owns the device memory of a context; the caller owns every host
  *     array it passes and keeps it alive for the duration of the call.
  *   - Calls on one context are not thread-safe; different contexts are independent.
@@ -45,10 +46,11 @@ typedef enum {
   ILG_E_STATE = 6     /* call out of order (e.g. step before init/set_state) */
 } ilg_status;
 
-typedef enum { ILG_D1Q3 = 1, ILG_D2Q5 = 2 } ilg_lattice;
+typedef enum { ILG_D1Q3 = 1, ILG_D2Q5 = 2, ILG_D2Q9 = 3 } ilg_lattice;
 
 /* Parameters of one lattice (Sec. II-V).
- *   lattice        ILG_D1Q3 or ILG_D2Q5
+ *   lattice        ILG_D1Q3, ILG_D2Q5 or ILG_D2Q9 (D2Q9: contexts and the comparator;
+ *                  batches take D1Q3 rings, the server D2Q5 lattices, temporal blocking D2Q5)
  *   Lx, Ly         periodic extent, >= 3 each (Ly is ignored and taken as 1 for D1Q3);
  *                  Lx * Ly < 2^32
  *   n0, amp        initial state (Sec. V): see init_weighted
@@ -60,7 +62,11 @@ typedef enum { ILG_D1Q3 = 1, ILG_D2Q5 = 2 } ilg_lattice;
  *   omega_eff      in (0, 2]: <= 1 collision fraction omega* = omega_eff without flip;
  *                  > 1 flip on and omega* = 2 - omega_eff, so omega^j = omega_eff
  *   theta          D1Q3 weights (1-theta, theta/2, theta/2), theta in (0, 1);
- *                  D2Q5 weights (1-2 theta, theta/2 x4), theta in (0, 1/2]
+ *                  D2Q5 weights (1-2 theta, theta/2 x4), theta in (0, 1/2];
+ *                  D2Q9 weights the products of the D1Q3 ones in x and y: (1-theta)^2,
+ *                  theta (1-theta)/2 x4 (axis), theta^2/4 x4 (diagonal), theta in (0, 1);
+ *                  its moving particles split binomially into axis and diagonal ones
+ *                  with P = 4 w_axis / (1 - w_0) before their directions are drawn
  *   seed, replica  Philox key and the replica word of every counter
  *   sampler        how the collision draws its random decisions (same law, different bits):
  *                  ILG_SAMPLER_BINOMIAL (0): per velocity one binomial draw of the

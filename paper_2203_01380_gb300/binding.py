@@ -23,7 +23,8 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 ILG_OK, ILG_E_INVALID, ILG_E_OOM, ILG_E_OVERFLOW, ILG_E_CUDA, ILG_E_TIMEOUT, ILG_E_STATE = range(7)
-D1Q3, D2Q5 = 1, 2
+D1Q3, D2Q5, D2Q9 = 1, 2, 3
+NUM_VEL = {D1Q3: 3, D2Q5: 5, D2Q9: 9}
 STATUS_NAMES = {0: "ILG_OK", 1: "ILG_E_INVALID", 2: "ILG_E_OOM", 3: "ILG_E_OVERFLOW", 4: "ILG_E_CUDA",
                 5: "ILG_E_TIMEOUT", 6: "ILG_E_STATE"}
 
@@ -131,7 +132,7 @@ SAMPLER_BINOMIAL, SAMPLER_PARTICLE = 0, 1
 
 def make_params(lattice, Lx, Ly=1, n0=10.0, amp=0.0, mode_mx=0, mode_my=0, init_weighted=0,
                 omega_eff=1.0, theta=1.0 / 3.0, seed=0, replica=0, sampler=0, **_ignored) -> Params:
-    return Params(int(lattice), int(Lx), int(Ly if lattice == D2Q5 else 1), int(mode_mx), int(mode_my),
+    return Params(int(lattice), int(Lx), int(Ly if lattice != D1Q3 else 1), int(mode_mx), int(mode_my),
                   int(init_weighted), float(n0), float(amp), float(omega_eff), float(theta), int(seed),
                   int(replica), int(sampler))
 
@@ -141,7 +142,7 @@ class Lattice:
 
     def __init__(self, lattice, Lx, Ly=1, stream=None, **kw):
         self.params = make_params(lattice, Lx, Ly, **kw)
-        self.Q = 3 if lattice == D1Q3 else 5
+        self.Q = NUM_VEL[lattice]
         self.Lx, self.Ly = self.params.Lx, self.params.Ly
         self.stream = stream_handle(stream)
         h = _vp()
@@ -392,9 +393,9 @@ class LB:
 
     def __init__(self, lattice, Lx, Ly=1, n0=10.0, amp=0.0, mode_mx=0, mode_my=0, init_weighted=0,
                  omega_j=1.0, omega=1.0, theta=1.0 / 3.0, stream=None, **_ignored):
-        self.params = LBParams(int(lattice), int(Lx), int(Ly if lattice == D2Q5 else 1), int(mode_mx), int(mode_my),
+        self.params = LBParams(int(lattice), int(Lx), int(Ly if lattice != D1Q3 else 1), int(mode_mx), int(mode_my),
                                int(init_weighted), float(n0), float(amp), float(omega_j), float(omega), float(theta))
-        self.Q = 3 if lattice == D1Q3 else 5
+        self.Q = NUM_VEL[lattice]
         self.Lx, self.Ly = self.params.Lx, self.params.Ly
         h = _vp()
         st = _lib.ilg_lb_create(ctypes.byref(self.params), _vp(stream_handle(stream)), ctypes.byref(h))

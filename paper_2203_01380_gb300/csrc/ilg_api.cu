@@ -18,7 +18,7 @@ struct ilg_ctx {
   ilg_params p{};
   int Q = 0;
   uint32_t flip = 0;
-  uint64_t P_omega = 0, P_rest = 0;
+  uint64_t P_omega = 0, P_rest = 0, P_axis = 0;  // P_axis: D2Q9 axis share
   cudaStream_t stream = nullptr;
   int device = 0;
   int sms = 0;
@@ -63,7 +63,7 @@ ilg_status cuda_fail(ilg_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
   } while (0)
 
-int num_vel(int lattice) { return lattice == ILG_D1Q3 ? 3 : 5; }
+int num_vel(int lattice) { return lattice == ILG_D1Q3 ? 3 : (lattice == ILG_D2Q5 ? 5 : 9); }
 
 uint32_t prob_mode(uint64_t P) {
   if (P == 0) return kNever;
@@ -75,16 +75,18 @@ uint32_t prob_mode(uint64_t P) {
 
 namespace ilg {
 std::string validate_params(const ilg_params& p) {
-  if (p.lattice != ILG_D1Q3 && p.lattice != ILG_D2Q5) return "lattice must be ILG_D1Q3 or ILG_D2Q5";
+  if (p.lattice != ILG_D1Q3 && p.lattice != ILG_D2Q5 && p.lattice != ILG_D2Q9)
+    return "lattice must be ILG_D1Q3, ILG_D2Q5 or ILG_D2Q9";
   if (p.sampler != ILG_SAMPLER_BINOMIAL && p.sampler != ILG_SAMPLER_PARTICLE)
     return "sampler must be ILG_SAMPLER_BINOMIAL or ILG_SAMPLER_PARTICLE";
   const uint64_t Ly = p.lattice == ILG_D1Q3 ? 1 : p.Ly;
   if (p.Lx < 3) return "Lx must be >= 3";
-  if (p.lattice == ILG_D2Q5 && p.Ly < 3) return "Ly must be >= 3";
+  if (p.lattice != ILG_D1Q3 && p.Ly < 3) return "Ly must be >= 3";
   if (uint64_t(p.Lx) * Ly >= (uint64_t(1) << 32)) return "Lx * Ly must be below 2^32";
   if (!(p.omega_eff > 0.0 && p.omega_eff <= 2.0)) return "omega_eff must lie in (0, 2]";
   if (p.lattice == ILG_D1Q3 && !(p.theta > 0.0 && p.theta < 1.0)) return "theta must lie in (0, 1) on D1Q3";
   if (p.lattice == ILG_D2Q5 && !(p.theta > 0.0 && p.theta <= 0.5)) return "theta must lie in (0, 1/2] on D2Q5";
+  if (p.lattice == ILG_D2Q9 && !(p.theta > 0.0 && p.theta < 1.0)) return "theta must lie in (0, 1) on D2Q9";
   if (!(p.n0 >= 0.0) || !std::isfinite(p.n0)) return "n0 must be finite and >= 0";
   if (!std::isfinite(p.amp)) return "amp must be finite";
   if (p.mode_mx != 0 && p.mode_my != 0) return "the initial sine must be an axis mode";
@@ -127,6 +129,7 @@ StepArgs step_args(const ilg_ctx* c) {
   a.flip = c->flip;
   a.omega_mode = prob_mode(c->P_omega);
   a.rest_mode = prob_mode(c->P_rest);
+  a.axis_mode = prob_mode(c->P_axis);
   a.particle = c->p.sampler == ILG_SAMPLER_PARTICLE ? 1u : 0u;
   a.general = c->general | a.particle;
   a.key0 = uint32_t(c->p.seed);
@@ -175,7 +178,7 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
   if (c->p.lattice == ILG_D1Q3) c->p.Ly = 1;
   c->Q = num_vel(c->p.lattice);
   c->stream = static_cast<cudaStream_t>(stream);
-  double w[5];
+  double w[9];
   weights(c->p.lattice, c->p.theta, w);
   double omega_star = c->p.omega_eff;
   if (c->p.omega_eff > 1.0) {
@@ -185,6 +188,7 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
   c->omega_star = omega_star;
   c->P_omega = quantise_probability(omega_star);
   c->P_rest = quantise_probability(w[0]);
+  c->P_axis = c->Q == 9 ? quantise_probability(axis_share(c->p.theta)) : 0;
   c->nodes = size_t(c->p.Lx) * c->p.Ly;
 
   auto bail = [&](cudaError_t e, const char* what) {
@@ -202,16 +206,18 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
     e = cudaMalloc(&c->buf[b], state_bytes);
     if (e != cudaSuccess) return bail(e, "cudaMalloc state");
   }
-  static_assert(kBlockWords == kDevBlockWords, "table block layout");
-  if ((e = cudaMalloc(&c->d_tables, sizeof(uint32_t) * kBlockWords)) != cudaSuccess) return bail(e, "cudaMalloc tables");
+  static_assert(kBlockWords == kDevBlockWords && kBlockWords9 == kDevBlockWords9, "table block layout");
+  const size_t block_words = c->Q == 9 ? kBlockWords9 : kBlockWords;
+  if ((e = cudaMalloc(&c->d_tables, sizeof(uint32_t) * block_words)) != cudaSuccess) return bail(e, "cudaMalloc tables");
   if ((e = cudaMalloc(&c->d_fail, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc flag");
   if ((e = cudaMalloc(&c->d_col, sizeof(unsigned long long) * c->p.Lx)) != cudaSuccess) return bail(e, "cudaMalloc sums");
   if ((e = cudaMalloc(&c->d_row, sizeof(unsigned long long) * c->p.Ly)) != cudaSuccess) return bail(e, "cudaMalloc sums");
   if ((e = cudaMalloc(&c->d_mass, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc mass");
   if ((e = cudaMallocHost(&c->h_word, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMallocHost");
 
-  std::vector<uint32_t> tables(kBlockWords, 0u);
-  build_table_block(c->Q, c->p.sampler, c->P_omega, c->P_rest, tables.data());
+  std::vector<uint32_t> tables(block_words, 0u);
+  build_table_block(c->Q, c->p.sampler, c->P_omega, c->P_rest, c->P_axis, tables.data());
+  if ((e = prepare_step9_kernel()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   if ((e = prepare_step_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   if ((e = prepare_step_vec_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   e = cudaMemcpyAsync(c->d_tables, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice, c->stream);
@@ -353,7 +359,7 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   const StepArgs a = step_args(c);
   // high occupations and the particle sampler go straight to the general collision
   // (node-parallel kernel)
-  const bool vec = !a.general && (c->p.Lx % step_vec_width()) == 0;
+  const bool vec = c->Q != 9 && !a.general && (c->p.Lx % step_vec_width()) == 0;
   const int grid = vec ? vec_grid(c) : step_grid(c, 3);
   const int cur0 = c->cur;
   const uint64_t t0 = c->t;
@@ -376,10 +382,11 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
     }
   }
   while (t < t0 + T) {
-    cudaError_t e = vec ? launch_step_vec(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid,
-                                          c->stream)
-                        : launch_step(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid,
-                                      c->stream);
+    cudaError_t e = c->Q == 9 ? launch_step9(a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid, c->stream)
+                    : vec     ? launch_step_vec(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid,
+                                                c->stream)
+                              : launch_step(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid,
+                                            c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
     launch_t.push_back(t);
     t += 1;

@@ -135,7 +135,7 @@ ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, 
   for (uint32_t i = 0; i < n; ++i) {
     const ilg_params& q = b->p[i];
     ReplicaDesc& d = b->desc[i];
-    double w[5];
+    double w[9];
     weights(ILG_D1Q3, q.theta, w);
     const double omega_star = q.omega_eff > 1.0 ? 2.0 - q.omega_eff : q.omega_eff;
     const uint64_t Po = quantise_probability(omega_star), Pr = quantise_probability(w[0]);
@@ -150,7 +150,7 @@ ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, 
     d.state_off = b->total;
     b->total += 3 * size_t(q.Lx);
     b->Lmax = std::max(b->Lmax, q.Lx);
-    build_table_block(3, q.sampler, Po, Pr, tables.data() + size_t(i) * kBlockWords);
+    build_table_block(3, q.sampler, Po, Pr, 0, tables.data() + size_t(i) * kBlockWords);
   }
   // longest rings first
   std::vector<uint32_t> order(n);

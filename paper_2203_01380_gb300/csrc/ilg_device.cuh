@@ -9,8 +9,12 @@ namespace ilg {
 
 constexpr uint32_t kDevNmax = 64;
 constexpr uint32_t kDevAliasEntries = (kDevNmax + 1) * (kDevNmax + 2) / 2;  // rows n = 0..64
-// table block: alias table (thinning) | alias table (rest), one uint2 {thr, alias} per column
+// table block: alias table (thinning) | alias table (rest), one uint2 {thr, alias} per column;
+// D2Q9 lattices append the alias table of the axis share
 constexpr uint32_t kDevBlockWords = 2 * kDevAliasEntries * 2;
+// (rounded up to whole 16-byte vectors: the kernels stage the block as uint4)
+constexpr uint32_t kDevBlockWords9 = (3 * kDevAliasEntries * 2 + 3) / 4 * 4;
+static_assert(kDevBlockWords % 4 == 0 && kDevBlockWords9 % 4 == 0, "table blocks are staged as uint4");
 constexpr uint32_t kDevTagStep = 1u << 24;
 constexpr uint32_t kDevTagExt = 2u << 24;
 constexpr uint32_t kDevTagInit = 3u << 24;
@@ -30,6 +34,7 @@ struct StepArgs {
                          //    fail, or the particle sampler)
   uint32_t particle;     // 1: particle sampler (one word per particle, tag-4 stream); the
                          //    table block then holds the boundaries B_0..B_Q (uint64)
+  uint32_t axis_mode;    // D2Q9: kNever / kTable / kAlways for the axis share
   uint32_t key0, key1;   // Philox key = seed
   uint32_t replica;
   const uint32_t* tables;   // device, kDevBlockWords words (layout above)
@@ -279,40 +284,59 @@ __device__ __forceinline__ void collide_phased(const StepArgs& a, const uint32_t
 }
 
 // The collision of one node with the particle sampler: particle k of velocity i
-// (in the order i = 0..Q-1, k = 0..m_i-1) takes word d of the tag-4 stream
-// (d counting all particles of the node) and stays when u < B_0, otherwise goes
-// to the velocity j with B_j <= u < B_{j+1}.  s holds B_0..B_Q as 64-bit integers
-// (B_Q = 2^32).  Counts of picked particles at or above each boundary give the
-// arrivals without a dynamically indexed array.
+// (in the order i = 0..Q-1, k = 0..m_i-1) takes word d (its running index) of the
+// tag-4 stream and stays when u < B_0, otherwise goes to the velocity j with
+// B_j <= u < B_{j+1}.  s holds B_0..B_Q as 64-bit integers (B_Q = 2^32).
+// The loop runs over whole Philox blocks, so a warp computes its blocks together;
+// a word's velocity follows from the prefix sums of m, and counts of picked
+// particles at or above each prefix sum (each boundary) give the removals (the
+// arrivals) without a dynamically indexed array.
 template <int Q>
 __device__ void collide_particle(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
                                  const uint32_t (&m)[Q], uint32_t (&out)[Q]) {
+  // D1Q3 / D2Q5 keep the boundaries in registers; D2Q9 reads them from shared memory
+  // per comparison to spare registers
   const unsigned long long* B = reinterpret_cast<const unsigned long long*>(s);
-  unsigned long long bound[Q];
+  unsigned long long breg[Q <= 5 ? Q : 1];
 #pragma unroll
-  for (int k = 0; k < Q; ++k) bound[k] = B[k];
-  uint32_t ge[Q];  // ge[0]: picked particles; ge[k]: picked ones with u >= B_k
+  for (int k = 0; k < (Q <= 5 ? Q : 1); ++k) breg[k] = B[k];
+  auto bound = [&](int k) -> unsigned long long { if constexpr (Q <= 5) return breg[k]; else return B[k]; };
+  uint32_t start[Q];  // start[k]: running index of the first particle of velocity k
+  uint32_t N = 0;
 #pragma unroll
-  for (int k = 0; k < Q; ++k) ge[k] = 0;
-  uint32_t d = 0;
-  uint4 blk = make_uint4(0, 0, 0, 0);
+  for (int k = 0; k < Q; ++k) {
+    start[k] = N;
+    N += m[k];
+  }
+  uint32_t ge[Q];     // ge[0]: picked particles; ge[j]: picked ones with u >= B_j
+  uint32_t from[Q];   // from[0]: picked particles; from[k]: picked ones of velocity >= k
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    uint32_t picked = 0;
-    for (uint32_t k = 0; k < m[i]; ++k, ++d) {
-      if ((d & 3u) == 0) blk = philox_rk(make_uint4(node, t, a.replica, kDevTagParticle | (d >> 2)), a.rk);
-      const unsigned long long u = lane_of(blk, d & 3u);
-      if (u >= bound[0]) {
-        ++picked;
+  for (int k = 0; k < Q; ++k) ge[k] = from[k] = 0;
+  if (bound(0) < (1ull << 32)) {  // B_0 = 2^32: every particle stays, the words are not needed
+    for (uint32_t b = 0; 4 * b < N; ++b) {
+      const uint4 blk = philox_rk(make_uint4(node, t, a.replica, kDevTagParticle | b), a.rk);
 #pragma unroll
-        for (int j = 1; j < Q; ++j) ge[j] += u >= bound[j] ? 1u : 0u;
+      for (uint32_t q = 0; q < 4; ++q) {
+        const uint32_t d = 4 * b + q;
+        const unsigned long long u = lane_of(blk, q);
+        if (d < N && u >= bound(0)) {
+          ge[0] += 1;
+          from[0] += 1;
+#pragma unroll
+          for (int j = 1; j < Q; ++j) {
+            ge[j] += u >= bound(j) ? 1u : 0u;
+            from[j] += d >= start[j] ? 1u : 0u;
+          }
+        }
       }
     }
-    out[i] = m[i] - picked;
-    ge[0] += picked;
   }
 #pragma unroll
-  for (int j = 0; j < Q; ++j) out[j] += ge[j] - (j + 1 < Q ? ge[j + 1] : 0u);
+  for (int j = 0; j < Q; ++j) {
+    const uint32_t removed = from[j] - (j + 1 < Q ? from[j + 1] : 0u);
+    const uint32_t arrived = ge[j] - (j + 1 < Q ? ge[j + 1] : 0u);
+    out[j] = m[j] - removed + arrived;
+  }
 }
 
 // The general collision in whichever sampler the lattice uses.

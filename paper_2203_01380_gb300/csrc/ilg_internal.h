@@ -28,14 +28,21 @@ struct AliasEntry {
 };
 // device table block: alias(thinning) | alias(rest), AliasEntry each
 constexpr uint32_t kBlockWords = 2 * kAliasEntries * 2;
+// D2Q9: alias(thinning) | alias(rest) | alias(axis share)
+// (rounded up to whole 16-byte vectors)
+constexpr uint32_t kBlockWords9 = (3 * kAliasEntries * 2 + 3) / 4 * 4;
 
 void build_binomial_table(uint64_t P, uint32_t* T);
 void build_alias_table(uint64_t P, AliasEntry* out);
 uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap);
 uint64_t quantise_probability(double p);
 uint32_t general_path(int Q, double omega_star, double mean_occupation);
-void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t* B);
-void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_rest, uint32_t* block);
+void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis, uint64_t* B);
+// table block of a lattice (kBlockWords words, kBlockWords9 for D2Q9)
+void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis,
+                       uint32_t* block);
+// D2Q9: probability that a moving particle takes an axis velocity, 4 w_axis / (1 - w_0)
+double axis_share(double theta);
 void weights(int lattice, double theta, double* w);
 
 // Poisson tables of the initial state, one per (velocity class, phase residue).

@@ -103,13 +103,19 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a, uint16_t* __restr
     uint32_t r = 0;
     if (a.axis == 1) r = uint32_t((uint64_t(a.mode) * x) % a.period);
     else if (a.axis == 2) r = uint32_t((uint64_t(a.mode) * y) % a.period);
-    const uint4 b0 = philox(make_uint4(node, 0u, a.replica, kDevTagInit | 0u), a.key0, a.key1);
-    uint4 b1 = make_uint4(0, 0, 0, 0);
-    if (Q > 4) b1 = philox(make_uint4(node, 0u, a.replica, kDevTagInit | 1u), a.key0, a.key1);
-    const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    uint32_t W[(Q + 3) / 4 * 4];
+#pragma unroll
+    for (int b = 0; b < (Q + 3) / 4; ++b) {
+      const uint4 w = philox(make_uint4(node, 0u, a.replica, kDevTagInit | uint32_t(b)), a.key0, a.key1);
+      W[4 * b] = w.x;
+      W[4 * b + 1] = w.y;
+      W[4 * b + 2] = w.z;
+      W[4 * b + 3] = w.w;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const uint32_t cls = (a.weighted && i != 0) ? 1u : 0u;
+      // weight class of the velocity: rest, moving (D2Q9: axis, diagonal)
+      const uint32_t cls = !a.weighted || i == 0 ? 0u : (Q == 9 && i > 4 ? 2u : 1u);
       const uint32_t idx = cls * a.period + r;
       const uint32_t* T = a.table + a.offset[idx];
       const uint32_t K = a.count[idx];
@@ -128,7 +134,8 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a, uint16_t* __restr
 
 cudaError_t launch_init(int Q, const InitArgs& a, uint16_t* out, int grid, cudaStream_t s) {
   if (Q == 3) init_kernel<3><<<grid, 256, 0, s>>>(a, out);
-  else init_kernel<5><<<grid, 256, 0, s>>>(a, out);
+  else if (Q == 5) init_kernel<5><<<grid, 256, 0, s>>>(a, out);
+  else init_kernel<9><<<grid, 256, 0, s>>>(a, out);
   return cudaGetLastError();
 }
 
@@ -169,7 +176,8 @@ __global__ void __launch_bounds__(256) sums_kernel(const uint16_t* __restrict__ 
 cudaError_t launch_sums(int Q, const uint16_t* in, uint32_t Lx, uint32_t Ly, unsigned long long* col,
                         unsigned long long* row, int want_rows, cudaStream_t s) {
   dim3 grid((Lx + 255) / 256, (Ly + kSumRows - 1) / kSumRows);
-  if (Q == 3) sums_kernel<3><<<grid, 256, 0, s>>>(in, Lx, Ly, col, row, want_rows);
+  if (Q == 9) sums_kernel<9><<<grid, 256, 0, s>>>(in, Lx, Ly, col, row, want_rows);
+  else if (Q == 3) sums_kernel<3><<<grid, 256, 0, s>>>(in, Lx, Ly, col, row, want_rows);
   else sums_kernel<5><<<grid, 256, 0, s>>>(in, Lx, Ly, col, row, want_rows);
   return cudaGetLastError();
 }

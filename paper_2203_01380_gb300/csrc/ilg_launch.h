@@ -15,7 +15,7 @@ struct InitArgs {
   uint32_t axis;      // 0 no sine mode, 1 along x, 2 along y
   uint32_t mode;      // wave number reduced to [0, period)
   uint32_t period;    // Lx, Ly, or 1
-  uint32_t weighted;  // 1: classes rest / moving
+  uint32_t weighted;  // 1: classes rest / moving (D2Q9: rest / axis / diagonal)
   uint32_t key0, key1, replica;
   const uint32_t* offset;  // [classes * period]
   const uint32_t* count;   // [classes * period]
@@ -34,6 +34,9 @@ cudaError_t prepare_step_tb_kernel(uint32_t B, uint32_t Tb);
 cudaError_t launch_step_tb(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t0, uint32_t Tb,
                            uint32_t B, unsigned long long* fail, int grid, cudaStream_t s);
 cudaError_t launch_init(int Q, const InitArgs& a, uint16_t* out, int grid, cudaStream_t s);
+cudaError_t prepare_step9_kernel();  // D2Q9 (ilg_d2q9.cu)
+cudaError_t launch_step9(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t, unsigned long long* fail,
+                         int grid, cudaStream_t s);
 cudaError_t launch_sums(int Q, const uint16_t* in, uint32_t Lx, uint32_t Ly, unsigned long long* col,
                         unsigned long long* row, int want_rows, cudaStream_t s);
 cudaError_t launch_project(const unsigned long long* col, const unsigned long long* row, uint32_t Lx,

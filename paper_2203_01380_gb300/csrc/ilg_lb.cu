@@ -28,7 +28,8 @@ constexpr uint32_t kLbChunk = 4096;    // entries per partial of a projection
 
 struct LbCoef {
   double cr;   // omega w_0
-  double cm;   // omega w_m
+  double cm;   // omega w_m (moving, D2Q9: axis)
+  double cd;   // D2Q9: omega w_diagonal
   double l2;   // 1 - omega
   double a1;   // ((1 - omega) + (1 - omega^j)) / 2
   double a2;   // ((1 - omega) - (1 - omega^j)) / 2
@@ -50,7 +51,8 @@ __global__ void __launch_bounds__(kLbThreads) lb_step_kernel(LbCoef k, const dou
 #pragma unroll
       for (int i = 0; i < Q; ++i) f[i] = in[i * plane + node];
       double rho = f[0] + f[1] + f[2];
-      if constexpr (Q == 5) rho = rho + f[3] + f[4];
+      if constexpr (Q >= 5) rho = rho + f[3] + f[4];
+      if constexpr (Q == 9) rho = rho + f[5] + f[6] + f[7] + f[8];
       const double c = k.cm * rho;
       const double p0 = fma(k.l2, f[0], k.cr * rho);
       const double p1 = fma(k.a1, f[1], fma(k.a2, f[2], c));
@@ -60,11 +62,23 @@ __global__ void __launch_bounds__(kLbThreads) lb_step_kernel(LbCoef k, const dou
       out[node] = p0;
       out[plane + row + xp] = p1;
       out[2 * plane + row + xm] = p2;
-      if constexpr (Q == 5) {
+      if constexpr (Q >= 5) {
         const double p3 = fma(k.a1, f[3], fma(k.a2, f[4], c));
         const double p4 = fma(k.a1, f[4], fma(k.a2, f[3], c));
         out[3 * plane + size_t(yp) * Lx + x] = p3;
         out[4 * plane + size_t(ym) * Lx + x] = p4;
+      }
+      if constexpr (Q == 9) {
+        // diagonal pairs (+1,+1)/(-1,-1) and (+1,-1)/(-1,+1)
+        const double cdr = k.cd * rho;
+        const double p5 = fma(k.a1, f[5], fma(k.a2, f[6], cdr));
+        const double p6 = fma(k.a1, f[6], fma(k.a2, f[5], cdr));
+        const double p7 = fma(k.a1, f[7], fma(k.a2, f[8], cdr));
+        const double p8 = fma(k.a1, f[8], fma(k.a2, f[7], cdr));
+        out[5 * plane + size_t(yp) * Lx + xp] = p5;
+        out[6 * plane + size_t(ym) * Lx + xm] = p6;
+        out[7 * plane + size_t(ym) * Lx + xp] = p7;
+        out[8 * plane + size_t(yp) * Lx + xm] = p8;
       }
     }
   }
@@ -84,7 +98,10 @@ __global__ void __launch_bounds__(kLbThreads) lb_init_kernel(const double* __res
     if (axis == 1) r = uint32_t((uint64_t(mode) * x) % period);
     else if (axis == 2) r = uint32_t((uint64_t(mode) * y) % period);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) out[i * plane + node] = lam[((weighted && i != 0) ? period : 0u) + r];
+    for (int i = 0; i < Q; ++i) {
+      const uint32_t cls = !weighted || i == 0 ? 0u : (Q == 9 && i > 4 ? 2u : 1u);
+      out[i * plane + node] = lam[cls * period + r];
+    }
   }
 }
 
@@ -336,15 +353,16 @@ ilg_status ilg_lb_create(const ilg_lb_params* params, void* stream, ilg_lb** out
   if (!(p.omega >= 0.0 && p.omega <= 2.0)) return lb_fail(nullptr, ILG_E_INVALID, "omega must lie in [0, 2]");
   ilg_lb* b = new ilg_lb();
   b->p = p;
-  b->Q = p.lattice == ILG_D1Q3 ? 3 : 5;
+  b->Q = p.lattice == ILG_D1Q3 ? 3 : (p.lattice == ILG_D2Q5 ? 5 : 9);
   b->Ly = p.lattice == ILG_D1Q3 ? 1 : p.Ly;
   b->p.Ly = b->Ly;
   b->nodes = size_t(p.Lx) * b->Ly;
   b->stream = static_cast<cudaStream_t>(stream);
-  double w[5];
+  double w[9];
   ilg::weights(p.lattice, p.theta, w);
   const double l2 = 1.0 - p.omega, lj = 1.0 - p.omega_j;
-  b->coef = LbCoef{p.omega * w[0], p.omega * w[1], l2, 0.5 * (l2 + lj), 0.5 * (l2 - lj)};
+  b->coef = LbCoef{p.omega * w[0], p.omega * w[1], b->Q == 9 ? p.omega * w[5] : 0.0, l2, 0.5 * (l2 + lj),
+                   0.5 * (l2 - lj)};
   b->chunks = (b->Ly + kLbRowChunk - 1) / kLbRowChunk;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -388,7 +406,7 @@ ilg_status ilg_lb_init(ilg_lb* b) {
   if (!b) return ILG_E_INVALID;
   const ilg_params g = as_gas(b->p);
   const uint32_t period = ilg::initial_period(g);
-  const int classes = b->p.init_weighted ? 2 : 1;
+  const int classes = b->p.init_weighted ? (b->Q == 9 ? 3 : 2) : 1;
   std::vector<double> lam(size_t(classes) * period);
   for (int c = 0; c < classes; ++c)
     for (uint32_t r = 0; r < period; ++r) {
@@ -412,8 +430,11 @@ ilg_status ilg_lb_init(ilg_lb* b) {
     if (b->Q == 3)
       lb_init_kernel<3><<<lb_grid(b), kLbThreads, 0, b->stream>>>(d_lam, period, axis, mode, b->p.init_weighted,
                                                                   b->f[b->cur], b->p.Lx, b->Ly);
-    else
+    else if (b->Q == 5)
       lb_init_kernel<5><<<lb_grid(b), kLbThreads, 0, b->stream>>>(d_lam, period, axis, mode, b->p.init_weighted,
+                                                                  b->f[b->cur], b->p.Lx, b->Ly);
+    else
+      lb_init_kernel<9><<<lb_grid(b), kLbThreads, 0, b->stream>>>(d_lam, period, axis, mode, b->p.init_weighted,
                                                                   b->f[b->cur], b->p.Lx, b->Ly);
     e = cudaGetLastError();
   }
@@ -452,8 +473,10 @@ ilg_status ilg_lb_step(ilg_lb* b, uint32_t T) {
   for (uint32_t k = 0; k < T; ++k) {
     if (b->Q == 3)
       lb_step_kernel<3><<<grid, kLbThreads, 0, b->stream>>>(b->coef, b->f[b->cur], b->f[b->cur ^ 1], b->p.Lx, b->Ly);
-    else
+    else if (b->Q == 5)
       lb_step_kernel<5><<<grid, kLbThreads, 0, b->stream>>>(b->coef, b->f[b->cur], b->f[b->cur ^ 1], b->p.Lx, b->Ly);
+    else
+      lb_step_kernel<9><<<grid, kLbThreads, 0, b->stream>>>(b->coef, b->f[b->cur], b->f[b->cur ^ 1], b->p.Lx, b->Ly);
     LB_CUDA(b, cudaGetLastError(), "lattice Boltzmann step");
     b->cur ^= 1;
     b->t += 1;
@@ -478,14 +501,16 @@ ilg_status ilg_lb_observables(ilg_lb* b, const int32_t* modes, uint32_t nmodes, 
   const double* f = b->f[b->cur];
   const dim3 pg((Lx + kLbThreads - 1) / kLbThreads, b->chunks);
   if (b->Q == 3) lb_colpart_kernel<3><<<pg, kLbThreads, 0, b->stream>>>(f, Lx, Ly, b->d_part);
-  else lb_colpart_kernel<5><<<pg, kLbThreads, 0, b->stream>>>(f, Lx, Ly, b->d_part);
+  else if (b->Q == 5) lb_colpart_kernel<5><<<pg, kLbThreads, 0, b->stream>>>(f, Lx, Ly, b->d_part);
+  else lb_colpart_kernel<9><<<pg, kLbThreads, 0, b->stream>>>(f, Lx, Ly, b->d_part);
   LB_CUDA(b, cudaGetLastError(), "column sums");
   lb_colsum_kernel<<<pg.x, kLbThreads, 0, b->stream>>>(b->d_part, Lx, b->chunks, b->d_col);
   LB_CUDA(b, cudaGetLastError(), "column sums");
   if (any_y) {
     const int rg = int(Ly < uint32_t(b->sms) * 8 ? Ly : uint32_t(b->sms) * 8);
     if (b->Q == 3) lb_rowsum_kernel<3><<<rg, kLbThreads, 0, b->stream>>>(f, Lx, Ly, b->d_row);
-    else lb_rowsum_kernel<5><<<rg, kLbThreads, 0, b->stream>>>(f, Lx, Ly, b->d_row);
+    else if (b->Q == 5) lb_rowsum_kernel<5><<<rg, kLbThreads, 0, b->stream>>>(f, Lx, Ly, b->d_row);
+    else lb_rowsum_kernel<9><<<rg, kLbThreads, 0, b->stream>>>(f, Lx, Ly, b->d_row);
     LB_CUDA(b, cudaGetLastError(), "row sums");
   }
   if (nmodes)

@@ -46,10 +46,11 @@ extern "C" ilg_status ilg_observables_noalloc(int32_t lattice, uint32_t Lx, uint
                                               const int32_t* modes, uint32_t nmodes, void* stream,
                                               uint64_t* mass, double* re, double* im, double* amp,
                                               double* Sk) {
-  if (lattice != ILG_D1Q3 && lattice != ILG_D2Q5) return context_free_fail(ILG_E_INVALID, "bad lattice");
+  if (lattice != ILG_D1Q3 && lattice != ILG_D2Q5 && lattice != ILG_D2Q9)
+    return context_free_fail(ILG_E_INVALID, "bad lattice");
   if (lattice == ILG_D1Q3) Ly = 1;
   if (!state) return context_free_fail(ILG_E_INVALID, "state is NULL");
-  if (Lx < 3 || (lattice == ILG_D2Q5 && Ly < 3)) return context_free_fail(ILG_E_INVALID, "Lx and Ly must be >= 3");
+  if (Lx < 3 || (lattice != ILG_D1Q3 && Ly < 3)) return context_free_fail(ILG_E_INVALID, "Lx and Ly must be >= 3");
   if (Lx > kMaxSide || Ly > kMaxSide)
     return context_free_fail(ILG_E_INVALID, "ilg_observables_noalloc: Lx and Ly are limited to 32768 by its static scratch");
   if (nmodes > kMaxModes)
@@ -80,7 +81,7 @@ extern "C" ilg_status ilg_observables_noalloc(int32_t lattice, uint32_t Lx, uint
     base = g_scratch_ptr[dev];
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int Q = lattice == ILG_D1Q3 ? 3 : 5;
+  const int Q = lattice == ILG_D1Q3 ? 3 : (lattice == ILG_D2Q5 ? 5 : 9);
   unsigned long long* col = base + kColOff;
   unsigned long long* row = base + kRowOff;
   unsigned long long* d_mass = base + kMassOff;

@@ -185,7 +185,7 @@ bool admit(ilg_server* s, const Request& rq, Resident* out, cudaError_t* cerr, s
     s->arena.release(r.off_tab, tab_bytes);
     return false;
   }
-  double w[5];
+  double w[9];
   weights(ILG_D2Q5, rq.p.theta, w);
   const double omega_star = rq.p.omega_eff > 1.0 ? 2.0 - rq.p.omega_eff : rq.p.omega_eff;
   const uint64_t Po = quantise_probability(omega_star), Pr = quantise_probability(w[0]);
@@ -195,7 +195,7 @@ bool admit(ilg_server* s, const Request& rq, Resident* out, cudaError_t* cerr, s
   r.omega_mode = mode_of(Po);
   r.rest_mode = mode_of(Pr);
   std::vector<uint32_t> tables(kBlockWords, 0u);
-  build_table_block(5, rq.p.sampler, Po, Pr, tables.data());
+  build_table_block(5, rq.p.sampler, Po, Pr, 0, tables.data());
   std::vector<uint32_t> init(init_words);
   std::copy(it.offset.begin(), it.offset.end(), init.begin());
   std::copy(it.count.begin(), it.count.end(), init.begin() + it.offset.size());

@@ -111,10 +111,24 @@ uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap) {
 // B_{j+1} = B_0 + floor(P_omega (P_rest (Q-1) + j (2^32 - P_rest)) / ((Q-1) 2^32))
 // for j = 0..Q-1, so a picked particle goes to rest with P_rest / 2^32 and to each
 // moving velocity with an equal share of the rest; B_Q = 2^32.
-void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t* B) {
+void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis, uint64_t* B) {
   typedef unsigned __int128 u128;
   const u128 two32 = u128(1) << 32;
   B[0] = uint64_t(two32 - P_omega);
+  if (Q == 9) {
+    // D2Q9: a picked particle goes to rest with P_rest / 2^32, to each axis velocity
+    // with (1 - P_rest / 2^32) (P_axis / 2^32) / 4 and to each diagonal one with
+    // (1 - P_rest / 2^32) (1 - P_axis / 2^32) / 4; cumulative shares in units of
+    // 1 / (4 2^64)
+    const u128 den = u128(4) << 64;
+    u128 cum = u128(4) * P_rest * two32;
+    for (int j = 0; j < 9; ++j) {
+      if (j >= 1 && j <= 4) cum += (two32 - P_rest) * u128(P_axis);
+      if (j >= 5) cum += (two32 - P_rest) * (two32 - P_axis);
+      B[j + 1] = B[0] + uint64_t((u128(P_omega) * cum) / den);
+    }
+    return;
+  }
   const u128 den = u128(uint32_t(Q - 1)) << 32;
   for (int j = 0; j < Q; ++j) {
     const u128 num = u128(P_omega) * (u128(P_rest) * uint32_t(Q - 1) + u128(uint32_t(j)) * (two32 - P_rest));
@@ -124,11 +138,12 @@ void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t* B
 
 // The device table block of a lattice: the two alias tables (binomial sampler) or
 // the particle boundaries.
-void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_rest, uint32_t* block) {
-  std::fill(block, block + kBlockWords, 0u);
+void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis,
+                       uint32_t* block) {
+  std::fill(block, block + (Q == 9 ? kBlockWords9 : kBlockWords), 0u);
   if (sampler == ILG_SAMPLER_PARTICLE) {
-    uint64_t B[6] = {0, 0, 0, 0, 0, 0};
-    build_particle_bounds(Q, P_omega, P_rest, B);
+    uint64_t B[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    build_particle_bounds(Q, P_omega, P_rest, P_axis, B);
     std::memcpy(block, B, sizeof(B));
     return;
   }
@@ -136,6 +151,13 @@ void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_res
   AliasEntry* al = reinterpret_cast<AliasEntry*>(block);
   if (P_omega > 0 && P_omega < two32) build_alias_table(P_omega, al);
   if (P_rest > 0 && P_rest < two32) build_alias_table(P_rest, al + kAliasEntries);
+  if (Q == 9 && P_axis > 0 && P_axis < two32) build_alias_table(P_axis, al + 2 * kAliasEntries);
+}
+
+double axis_share(double theta) {
+  double w[9];
+  weights(ILG_D2Q9, theta, w);
+  return (4.0 * w[1]) / (1.0 - w[0]);
 }
 
 uint32_t general_path(int Q, double omega_star, double mean_occupation) {
@@ -153,6 +175,11 @@ void weights(int lattice, double theta, double* w) {
   if (lattice == ILG_D1Q3) {
     w[0] = 1.0 - theta;
     w[1] = w[2] = theta / 2.0;
+  } else if (lattice == ILG_D2Q9) {
+    // products of the D1Q3 weights in x and y: rest, four axis, four diagonal
+    w[0] = (1.0 - theta) * (1.0 - theta);
+    w[1] = w[2] = w[3] = w[4] = (theta * (1.0 - theta)) / 2.0;
+    w[5] = w[6] = w[7] = w[8] = (theta * theta) / 4.0;
   } else {
     w[0] = 1.0 - 2.0 * theta;
     w[1] = w[2] = w[3] = w[4] = theta / 2.0;
@@ -169,9 +196,9 @@ static double profile_sine(uint32_t r, uint32_t L) {
 double initial_mean(const ilg_params& p, int Q, int cls, uint32_t r, uint32_t L) {
   const double s = (p.amp != 0.0 && L != 0) ? profile_sine(r, L) : 0.0;
   if (p.init_weighted) {
-    double w[5];
+    double w[9];
     weights(p.lattice, p.theta, w);
-    const double wc = cls == 0 ? w[0] : w[1];
+    const double wc = cls == 0 ? w[0] : (cls == 1 ? w[1] : w[5]);
     return wc * (static_cast<double>(Q) * p.n0 + p.amp * s);
   }
   return p.n0 + (p.amp * s) / static_cast<double>(Q);
@@ -185,7 +212,7 @@ uint32_t initial_period(const ilg_params& p) {
 
 bool build_init_tables(const ilg_params& p, int Q, InitTables* out, std::string* err) {
   const uint32_t L = initial_period(p);  // period of the phase residue
-  const int classes = p.init_weighted ? 2 : 1;
+  const int classes = p.init_weighted ? (Q == 9 ? 3 : 2) : 1;
   out->period = L;
   out->classes = classes;
   out->offset.assign(size_t(classes) * L, 0);

@@ -19,6 +19,8 @@ Workloads (the paper uses no dataset; every input is generated):
   serve_d2q5     Poisson arrivals (200 / s) of D2Q5 requests, side log-uniform
                  in [64, 2048], steps log-uniform in [100, 10000], mean
                  occupation uniform in [5, 100], omega_eff 1.5, seed 5
+  large_d2q9     D2Q9 16384^2 (weights 4/9, 1/9, 1/36), mean 10 per velocity,
+                 omega_eff 1.8, 100 steps, seed 3
   lb_d2q5        lattice Boltzmann comparator on 16384^2 (D2Q5), initial f the
                  sweep's Poisson means (50 per velocity, sine amplitude 20 along
                  x), rates of the gas with omega_eff 1.8, 200 steps
@@ -29,7 +31,7 @@ from __future__ import annotations
 
 import numpy as np
 
-D1Q3, D2Q5 = 1, 2
+D1Q3, D2Q5, D2Q9 = 1, 2, 3
 
 RING_D1Q3 = dict(lattice=D1Q3, Lx=256, Ly=1, n0=30.0, amp=10.0, mode_mx=1, mode_my=0,
                  init_weighted=0, omega_eff=1.5, theta=1.0 / 3.0, seed=1, replica=0, steps=2000)
@@ -39,6 +41,8 @@ SWEEP_D2Q5 = [dict(lattice=D2Q5, Lx=1024, Ly=1024, n0=50.0, amp=20.0, mode_mx=1,
 LARGE_D2Q5 = dict(lattice=D2Q5, Lx=16384, Ly=16384, n0=10.0, amp=0.0, mode_mx=0, mode_my=0,
                   init_weighted=0, omega_eff=1.8, theta=1.0 / 3.0, seed=3, replica=0, steps=500)
 LARGE_MODES = [(m, 0) for m in range(1, 65)]
+LARGE_D2Q9 = dict(lattice=3, Lx=16384, Ly=16384, n0=10.0, amp=0.0, mode_mx=0, mode_my=0,
+                  init_weighted=0, omega_eff=1.8, theta=1.0 / 3.0, seed=3, replica=0, steps=100)
 LB_D2Q5 = dict(lattice=D2Q5, Lx=16384, Ly=16384, n0=50.0, amp=20.0, mode_mx=1, mode_my=0,
                init_weighted=0, omega_eff=1.8, theta=1.0 / 3.0, steps=200)
 ENSEMBLE_D1Q3 = dict(lattice=D1Q3, Lx=320, Ly=1, n0=100.0 / 3.0, amp=100.0, mode_mx=1, mode_my=0,
