@@ -139,16 +139,42 @@ def dist_setup(args):
     return world, rank, local
 
 
-def oracle_sample(cfg, side=512, steps=8):
+def oracle_sample(cfg, side=512, steps=8, x0=0, y0=0):
     """The oracle on a side x side window of the workload for `steps` steps
     (light-cone patch from its own initial state).  Returns (node updates, s)."""
     import oracle as O
     ref = O.Lattice(**cfg)
     t0 = time.perf_counter()
-    ref.window(0, 0, side, side, steps)
+    ref.window(x0, y0, side, side, steps)
     dt = time.perf_counter() - t0
     nu = sum((side + 2 * (steps - k)) ** 2 for k in range(steps))
     return nu, dt
+
+
+def oracle_worker(cfg, side, steps, x0, seconds):
+    """One process of the all-cores oracle sample: windows at x0, x0 + side, ...
+    until `seconds` have passed.  Returns (node updates, busy seconds)."""
+    nu, busy, k = 0, 0.0, 0
+    while busy < seconds:
+        n_, d_ = oracle_sample(cfg, side, steps, (x0 + k * side) % cfg["Lx"], 0)
+        nu += n_
+        busy += d_
+        k += 1
+    return nu, busy
+
+
+def oracle_all_cores(cfg, side, steps, seconds):
+    """The oracle, unchanged, in one process per host core (spawned: the parent may
+    already hold a CUDA context).  Returns (node updates per second, processes)."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(n) as pool:
+        pool.starmap(oracle_sample, [(cfg, 64, 2)] * n)  # load the oracle in every process
+        t0 = time.perf_counter()
+        res = pool.starmap(oracle_worker, [(cfg, side, steps, k * 997 * side, seconds) for k in range(n)])
+        wall = time.perf_counter() - t0
+    return sum(r[0] for r in res) / wall, n
 
 
 def alu_roofline(nodes, launch_ms, clocks):
@@ -386,24 +412,33 @@ def measure_serving(B, n_requests=200):
 
 
 def run_reference(args, cfg, world, rank):
+    """The oracle as the reference arm: every step runs one light-cone window per host
+    core, in parallel processes (spawned), on the same workload."""
     if rank != 0:
         return
+    import multiprocessing as mp
     side, steps = 512, 8
-    oracle_sample(cfg, 64, 2)  # build / load the oracle
-    for _ in range(args.warmup):
-        oracle_sample(cfg, side, steps)
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
     tot_nu, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        nu, dt = oracle_sample(cfg, side, steps)
-        tot_nu += nu
-        tot_t += dt
+    with ctx.Pool(n) as pool:
+        pool.starmap(oracle_sample, [(cfg, 64, 2)] * n)  # build / load the oracle everywhere
+        jobs = [(cfg, side, steps, (k * 997 * side) % cfg["Lx"], 0) for k in range(n)]
+        for _ in range(args.warmup):
+            pool.starmap(oracle_sample, jobs)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            res = pool.starmap(oracle_sample, jobs)
+            tot_t += time.perf_counter() - t0
+            tot_nu += sum(r[0] for r in res)
     v = tot_nu / tot_t / 1e9
-    sample = f"oracle light-cone window {side}x{side} after {steps} steps of the 16384^2 workload (its own initial state)"
+    sample = (f"oracle light-cone windows {side}x{side} after {steps} steps of the 16384^2 workload (its own "
+              f"initial state), one window per host core per step, {n} processes")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GNUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
             "data": "synthetic", "config": {"workload": "large_d2q5 (sampled)", "Lx": cfg["Lx"], "Ly": cfg["Ly"]},
-            "cpu_baseline": {"value": v, "unit": "GNUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "GNUPS", "cores": n, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "GNUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -546,8 +581,12 @@ def main():
             n_, d_ = oracle_sample(cfg, side, csteps)
             nu_c += n_
             dt_c += d_
-        cpu = {"value": nu_c / dt_c / 1e9, "unit": "GNUPS", "cores": 1, "kind": "oracle",
-               "sample": f"oracle (single thread) light-cone windows {side}x{side} after {csteps} steps of the same workload, ~10 s"}
+        rate, nproc = oracle_all_cores(cfg, side, csteps, 10.0)
+        cpu = {"value": rate / 1e9, "unit": "GNUPS", "cores": nproc, "kind": "oracle",
+               "sample": f"oracle light-cone windows {side}x{side} after {csteps} steps of the same workload, "
+                         f"one process per host core for ~10 s each",
+               "single_thread": {"value": nu_c / dt_c / 1e9, "unit": "GNUPS", "cores": 1,
+                                 "sample": f"the same windows in one thread, ~10 s"}}
 
     if rank == 0:
         line = {
