@@ -144,3 +144,16 @@ def test_comparator_d2q9_and_replica_mean(B):
     mean = acc / R
     chi2 = float((((mean - f) ** 2) / (f / R)).sum())
     assert stats.chi2.ppf(1e-6, f.size) < chi2 < stats.chi2.ppf(1 - 1e-6, f.size), chi2
+
+
+@pytest.mark.parametrize("Lx,Ly,steps", [(3, 3, 9), (65536, 3, 3), (3, 2051, 4), (5, 7, 12)])
+def test_extreme_extents(B, Lx, Ly, steps):
+    """Smallest lattice (every diagonal wraps onto itself), very long rows, very tall
+    columns: bit-exact against the oracle."""
+    cfg = dict(lattice=3, Lx=Lx, Ly=Ly, n0=6.0, omega_eff=1.5, seed=Lx + Ly)
+    ref = O.Lattice(**cfg)
+    with B.Lattice(**cfg) as lat:
+        lat.init()
+        lat.step(steps)
+        got, _ = lat.get_state()
+    assert np.array_equal(got, ref.run(ref.init(), 0, steps))

@@ -109,3 +109,25 @@ def test_ensemble_errors(B):
         bat.init()
         with pytest.raises(B.IlgError):
             bat.ensemble(4, mode=64)
+
+
+def test_ensemble_zero_steps_and_particle_sampler(B):
+    """T = 0 gives the statistics of the initial states alone; rings with the particle
+    sampler give records equal to the oracle's."""
+    L = 24
+    reps = [dict(lattice=1, Lx=L, n0=12.0, amp=8.0, mode_mx=1, omega_eff=1.3, seed=3, replica=i, sampler=1)
+            for i in range(5)]
+    with B.Batch(reps) as bat:
+        bat.init()
+        st0 = bat.ensemble(0, mode=1, record=True)
+        assert st0["record"].shape == (5, 1, 2)
+        st = bat.ensemble(6, mode=1, record=True)
+    for i, r in enumerate(reps):
+        lat = O.Lattice(**r)
+        s = lat.init()
+        _, _, _, res = lat.observables(s, [(1, 0)])
+        assert abs(st0["record"][i, 0, 1] - res[0]["im"]) <= 1e-12 * res[0]["scale"] + 1e-12
+        for t in range(6):
+            s = lat.step(s, t)
+        _, _, _, res = lat.observables(s, [(1, 0)])
+        assert abs(st["record"][i, 6, 1] - res[0]["im"]) <= 1e-12 * res[0]["scale"] + 1e-12

@@ -172,3 +172,23 @@ def test_gas_replica_mean_is_lattice_boltzmann(B, sampler):
     chi2 = float((((mean - f) ** 2) / (f / R)).sum())
     dof = f.size
     assert stats.chi2.ppf(1e-6, dof) < chi2 < stats.chi2.ppf(1 - 1e-6, dof), chi2
+
+
+@pytest.mark.parametrize("lattice,Lx,Ly", [(1, 3, 1), (2, 3, 3), (3, 3, 3), (3, 4, 7)])
+def test_smallest_lattices(B, lattice, Lx, Ly):
+    """Lattices of three nodes per side (neighbours coincide after wrapping) and a mode
+    at L/2 (its sine vanishes at every node)."""
+    f0 = np.random.default_rng(lattice + Lx).uniform(0.0, 20.0, size=(B.NUM_VEL[lattice], Ly if lattice != 1 else 1, Lx))
+    ora = OL.LB(lattice, Lx, Ly, omega_j=1.6, omega=0.4)
+    with B.LB(lattice, Lx, Ly, omega_j=1.6, omega=0.4) as gpu:
+        gpu.set_state(f0)
+        gpu.step(11)
+        f, _ = gpu.get_state()
+        modes = [(1, 0)] + ([(2, 0)] if Lx % 2 == 0 else [])
+        obs = gpu.observables(modes)
+    ref = ora.run(f0, 11)
+    assert np.abs(f - ref).max() <= 8e-15 * 21 * np.abs(f0).max()
+    M, res = ora.observables(f, modes)
+    assert abs(obs["mass"] - M) <= 1e-13 * M
+    for j in range(len(modes)):
+        assert abs(obs["re"][j] - res[j][0]) <= 1e-12 * M and abs(obs["im"][j] - res[j][1]) <= 1e-12 * M
