@@ -177,7 +177,11 @@ def oracle_all_cores(cfg, side, steps, seconds):
     return sum(r[0] for r in res) / wall, n
 
 
-def alu_roofline(nodes, launch_ms, clocks):
+KERNEL_NAMES = {"vec8": "step_vec_kernel<5, 8>", "vec4": "step_vec_kernel<5, 4>", "node": "step_kernel<5>",
+                "tb2": "step_tb_kernel (depth 2)", "tb4": "step_tb_kernel (depth 4)"}
+
+
+def alu_roofline(nodes, launch_ms, clocks, choice="vec8"):
     """The step kernel is bound by integer issue: OPS_PER_NU algorithmic int32
     operations per node update against 128 int32 lane-operations per SM per cycle
     at the SM clock measured during the run."""
@@ -185,7 +189,8 @@ def alu_roofline(nodes, launch_ms, clocks):
     peak = INT_LANES_PER_SM_CYCLE * SMS * mhz * 1e6 / 1e9          # Gop/s
     achieved = OPS_PER_NU * nodes / (launch_ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_BYTES_PER_LAUNCH, "kernel": "step_vec_kernel<5, 8>", "launch_ms": launch_ms,
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH if choice == "vec8" else None,
+            "kernel": KERNEL_NAMES.get(choice, choice), "launch_ms": launch_ms,
             "ops_per_node_update": OPS_PER_NU, "peak_clock_mhz": mhz}
 
 
@@ -198,6 +203,7 @@ def measure_batched(torch, B, dev):
     st = torch.cuda.Stream(dev)
     with B.Batch(reps, stream=st) as bat:
         bat.init()
+        tuning = bat.autotune(50)
         bat.run(20)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
@@ -221,7 +227,7 @@ def measure_batched(torch, B, dev):
             "value": v, "unit": "GNUPS", "ms": ms, "node_updates": nodes * T,
             "plain_per_ring_launch": {"value": vp, "unit": "GNUPS",
                                       "sample": "16 rings (evenly spaced in the list), init + 500 steps each, one context each, host wall clock"},
-            "speedup_vs_plain": v / vp}
+            "speedup_vs_plain": v / vp, "autotune": tuning}
 
 
 FP64_LANES_PER_SM_CYCLE = 2.0   # GB300 nominal 1.25 TFLOP/s fp64 = 2 fused multiply-add lanes per SM per cycle at 2070 MHz
@@ -275,6 +281,7 @@ def measure_ensemble(torch, B, dev):
     st = torch.cuda.Stream(dev)
     with B.Batch(reps, stream=st) as bat:
         bat.init()
+        tuning = bat.autotune(50)
         bat.ensemble(10)
         bat.init()
         torch.cuda.synchronize(dev)
@@ -295,7 +302,7 @@ def measure_ensemble(torch, B, dev):
             "amplitude": {"t0": float(amp[0]), "t_end": float(amp[-1]),
                           "sd_of_mean_t_end": float(math.sqrt(stats["var_im"][-1] / R) / (L / 2.0))},
             "diffusion": {"fitted": float(-slope / k2), "theory": D_theory, "fit": "ln <A(t)>, t in [200, 2000]"},
-            "structure_factor_t0_over_mass": float(stats["cov_re"][0] / (cfg["n0"] * 3 * L))}
+            "structure_factor_t0_over_mass": float(stats["cov_re"][0] / (cfg["n0"] * 3 * L)), "autotune": tuning}
 
 
 def measure_particle(torch, B, dev, side):
@@ -481,6 +488,7 @@ def main():
     lat = B.Lattice(**cfg, stream=stream)
     lat.init()
     nodes = cfg["Lx"] * cfg["Ly"]
+    tuning = lat.autotune(20)   # launch shape chosen by timing (outside the timed region)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -601,7 +609,8 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": launches,
-            "roofline": alu_roofline(nodes, launch_ms, clk.summary()),
+            "autotune": tuning,
+            "roofline": alu_roofline(nodes, launch_ms, clk.summary(), tuning["choice"]),
             "hbm": {"achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
                     "algorithmic_bytes_per_launch": nodes * BYTES_PER_NU, "peak_source": "MEASURED_PEAKS.json hbm_gbs"
                     if pk else "fallback 6800"},

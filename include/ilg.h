@@ -135,6 +135,34 @@ ilg_status ilg_step(ilg_ctx* ctx, uint32_t T);
  * ILG_E_OVERFLOW the state is the input of the failing launch. */
 ilg_status ilg_set_temporal_blocking(ilg_ctx* ctx, uint32_t depth);
 
+/* Autotuner.  Times the launch shapes that give the same bits on a copy of the
+ * current state (2 extra state buffers, freed before return) and keeps the fastest
+ * for later ilg_step calls:
+ *   candidate 0  row-tiled step, 8 nodes per thread (16-byte vectors), 3 blocks per SM
+ *   candidate 1  row-tiled step, 4 nodes per thread (8-byte vectors), 4 blocks per SM
+ *   candidate 2  node-parallel step, one node per thread
+ *   candidate 3, 4  temporal blocking of depth 2, 4 (D2Q5; the remainder of a call
+ *                takes the fastest of 0-2)
+ * Candidates that do not apply (row length, D2Q9, occupations that need the general
+ * collision) are skipped (ms_per_step < 0).  A choice that stops applying after
+ * ilg_set_state (e.g. occupations rise) falls back to the default.  trial_steps:
+ * steps per candidate (0: 20; at most 1000).  The state, the step counter and all
+ * results are unchanged.  ILG_E_OOM if the scratch does not fit.  Synchronous.
+ * ilg_set_temporal_blocking later overrides the depth. */
+typedef struct {
+  uint32_t choice;         /* index of the chosen candidate */
+  uint32_t tb_depth;       /* contexts: temporal blocking depth now in use (0: none) */
+  uint32_t threads;        /* threads per block of the choice */
+  uint32_t n;              /* candidates considered */
+  double ms_per_step[8];   /* measured ms per time step per candidate; < 0: not applicable */
+} ilg_tuning;
+
+ilg_status ilg_autotune(ilg_ctx* ctx, uint32_t trial_steps, ilg_tuning* out);
+/* Set the single-step kernel by hand: candidate 0, 1 or 2 as above, -1 the default.
+ * A candidate that does not apply to the current state falls back to the default;
+ * results are the same bits either way. */
+ilg_status ilg_set_step_kernel(ilg_ctx* ctx, int32_t candidate);
+
 /* Observables of the current state (Sec. V).  modes: nmodes pairs (mx, my), each an
  * axis mode (one of the two zero, not both).  For a mode along x with
  * D(x) = Lx*C(x) - M, C(x) = sum_y N(x,y), r = (mx*x) mod Lx:
@@ -193,6 +221,12 @@ ilg_status ilg_batch_get_state(ilg_batch* b, uint32_t i, uint16_t* host, size_t 
 ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record);
 ilg_status ilg_batch_observables(ilg_batch* b, int32_t mode, uint64_t* mass, double* amp);
 ilg_status ilg_batch_ensemble(ilg_batch* b, uint32_t T, int32_t mode, double* stats, double* record);
+/* Batch autotuner: times the block shapes 256, 512 and 1024 threads (candidates 0-2;
+ * ceil(L / threads) nodes of a ring per thread and step, as many blocks per SM as
+ * shared memory allows) for trial_steps steps (0: 50; at most 10000) on copies of all
+ * rings, and keeps the fastest for later runs.  States, step counters and results are
+ * unchanged.  out may be NULL.  Synchronous. */
+ilg_status ilg_batch_autotune(ilg_batch* b, uint32_t trial_steps, ilg_tuning* out);
 
 /* ---------------------------------------------------------------------------
  * Serving loop for D2Q5 lattice requests (continuous batching).  A worker thread

@@ -76,6 +76,29 @@ _lib.ilg_batch_get_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t,
 _lib.ilg_batch_run.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp]
 _lib.ilg_batch_observables.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
 _lib.ilg_batch_ensemble.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp, _vp]
+class Tuning(ctypes.Structure):
+    _fields_ = [("choice", ctypes.c_uint32), ("tb_depth", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("n", ctypes.c_uint32), ("ms_per_step", ctypes.c_double * 8)]
+
+
+CONTEXT_CANDIDATES = ("vec8", "vec4", "node", "tb2", "tb4")
+BATCH_CANDIDATES = ("threads256", "threads512", "threads1024")
+
+
+def _tuning_dict(t: Tuning, names) -> dict:
+    return dict(choice=names[t.choice], tb_depth=int(t.tb_depth), threads=int(t.threads),
+                ms_per_step={names[k]: (float(t.ms_per_step[k]) if t.ms_per_step[k] >= 0 else None)
+                             for k in range(t.n)})
+
+
+_lib.ilg_autotune.argtypes = [_vp, ctypes.c_uint32, ctypes.POINTER(Tuning)]
+_lib.ilg_autotune.restype = ctypes.c_int
+_lib.ilg_set_step_kernel.argtypes = [_vp, ctypes.c_int32]
+_lib.ilg_set_step_kernel.restype = ctypes.c_int
+_lib.ilg_batch_autotune.argtypes = [_vp, ctypes.c_uint32, ctypes.POINTER(Tuning)]
+_lib.ilg_batch_autotune.restype = ctypes.c_int
+
+
 class Result(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_uint32),
                 ("t", ctypes.c_uint64), ("mass", ctypes.c_uint64), ("amp", ctypes.c_double), ("Sk", ctypes.c_double),
@@ -201,6 +224,16 @@ class Lattice:
     def step(self, T: int):
         _check(_lib.ilg_step(self._h, int(T)), self._h)
 
+    def autotune(self, trial_steps: int = 20) -> dict:
+        """ilg_autotune: time the launch shapes on a copy of the state, keep the fastest."""
+        t = Tuning()
+        _check(_lib.ilg_autotune(self._h, int(trial_steps), ctypes.byref(t)), self._h)
+        return _tuning_dict(t, CONTEXT_CANDIDATES)
+
+    def set_step_kernel(self, candidate: int):
+        """ilg_set_step_kernel: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, -1 default."""
+        _check(_lib.ilg_set_step_kernel(self._h, int(candidate)), self._h)
+
     def set_temporal_blocking(self, depth: int):
         _check(_lib.ilg_set_temporal_blocking(self._h, int(depth)), self._h)
 
@@ -279,6 +312,12 @@ class Batch:
         return mass, amp
 
     ENSEMBLE_ROWS = ("mean_re", "mean_im", "var_re", "var_im", "cov_re", "cov_im")
+
+    def autotune(self, trial_steps: int = 50) -> dict:
+        """ilg_batch_autotune: time the block shapes on copies of the rings, keep the fastest."""
+        t = Tuning()
+        self._check(_lib.ilg_batch_autotune(self._h, int(trial_steps), ctypes.byref(t)))
+        return _tuning_dict(t, BATCH_CANDIDATES)
 
     def ensemble(self, T, mode=1, record=False):
         """T steps with the ensemble statistics of mode `mode` at t = 0..T (dict of

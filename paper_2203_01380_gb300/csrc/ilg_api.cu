@@ -37,6 +37,7 @@ struct ilg_ctx {
   uint32_t mode_cap = 0;
   uint32_t tb_depth = 0;                   // temporal blocking: steps per launch (0: off)
   uint32_t general = 0;                    // high occupation: general collision path at once
+  int kernel_choice = -1;                  // single-step kernel chosen by ilg_autotune (-1: default)
   double omega_star = 0;
   unsigned long long* h_word = nullptr;    // pinned 8-byte readback
   std::string err;
@@ -109,16 +110,16 @@ namespace {
 using ilg::validate_params;
 
 // node-parallel kernels: `per_sm` resident blocks of 256 threads on every SM
-int step_grid(const ilg_ctx* c, size_t per_sm = 4) {
+int step_grid(const ilg_ctx* c, size_t per_sm) {
   const size_t blocks = (c->nodes + 255) / 256;
   const size_t cap = size_t(c->sms) * per_sm;
   return int(blocks < cap ? blocks : cap);
 }
 
-// row-tiled step: one block per row at a time, three blocks per SM
-int vec_grid(const ilg_ctx* c) {
+// row-tiled step: one block per row at a time, per_sm blocks per SM
+int vec_grid(const ilg_ctx* c, size_t per_sm) {
   const size_t rows = c->p.Ly;
-  const size_t cap = size_t(c->sms) * 3;
+  const size_t cap = size_t(c->sms) * per_sm;
   return int(rows < cap ? rows : cap);
 }
 
@@ -282,7 +283,7 @@ ilg_status ilg_init(ilg_ctx* c) {
   a.offset = d_off;
   a.count = d_cnt;
   a.table = d_tab;
-  if ((e = launch_init(c->Q, a, c->buf[c->cur], step_grid(c), c->stream)) != cudaSuccess) {
+  if ((e = launch_init(c->Q, a, c->buf[c->cur], step_grid(c, 4), c->stream)) != cudaSuccess) {
     cleanup();
     return cuda_fail(c, e, "init kernel");
   }
@@ -351,6 +352,43 @@ ilg_status ilg_set_temporal_blocking(ilg_ctx* c, uint32_t depth) {
   return ILG_OK;
 }
 
+namespace {
+
+// Single-step kernels, in the order of the autotuner's candidates.
+enum : int { kKernelVec8 = 0, kKernelVec4 = 1, kKernelNode = 2 };
+
+bool kernel_applies(const ilg_ctx* c, const StepArgs& a, int kind) {
+  if (kind == kKernelNode) return true;
+  if (c->Q == 9 || a.general) return false;  // D2Q9 and the general path run node-parallel
+  return c->p.Lx % (kind == kKernelVec8 ? 8u : 4u) == 0;
+}
+
+// the kernel a step runs: the tuned one while it applies to the current state, else
+// the default (8-node vectors where the rows allow, node-parallel otherwise)
+int pick_kernel(const ilg_ctx* c, const StepArgs& a) {
+  if (c->kernel_choice >= 0 && kernel_applies(c, a, c->kernel_choice)) return c->kernel_choice;
+  return kernel_applies(c, a, kKernelVec8) ? kKernelVec8 : kKernelNode;
+}
+
+cudaError_t launch_single(const ilg_ctx* c, int kind, const StepArgs& a, const uint16_t* in, uint16_t* out,
+                          uint64_t t, unsigned long long* fail_word) {
+  if (c->Q == 9) return launch_step9(a, in, out, uint32_t(t), fail_word, step_grid(c, 3), c->stream);
+  if (kind == kKernelVec8)
+    return launch_step_vec(c->Q, a, in, out, uint32_t(t), fail_word, vec_grid(c, step_vec_blocks_per_sm(8)), c->stream,
+                           8);
+  if (kind == kKernelVec4)
+    return launch_step_vec(c->Q, a, in, out, uint32_t(t), fail_word, vec_grid(c, step_vec_blocks_per_sm(4)), c->stream,
+                           4);
+  return launch_step(c->Q, a, in, out, uint32_t(t), fail_word, step_grid(c, 3), c->stream);
+}
+
+int tb_grid(const ilg_ctx* c) {
+  const size_t tiles = size_t((c->p.Lx + kTbTile - 1) / kTbTile) * ((c->p.Ly + kTbTile - 1) / kTbTile);
+  return int(std::min<size_t>(tiles, size_t(c->sms) * 2));
+}
+
+}  // namespace
+
 ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   if (!c) return ILG_E_INVALID;
   if (!c->has_state) return fail(c, ILG_E_STATE, "no state: call ilg_init or ilg_set_state first");
@@ -359,8 +397,7 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   const StepArgs a = step_args(c);
   // high occupations and the particle sampler go straight to the general collision
   // (node-parallel kernel)
-  const bool vec = c->Q != 9 && !a.general && (c->p.Lx % step_vec_width()) == 0;
-  const int grid = vec ? vec_grid(c) : step_grid(c, 3);
+  const int kind = pick_kernel(c, a);
   const int cur0 = c->cur;
   const uint64_t t0 = c->t;
   // launches: blocks of tb_depth steps (temporal blocking), then single steps;
@@ -370,8 +407,7 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   uint64_t t = t0;
   const uint32_t tb = c->tb_depth;
   if (tb >= 2) {
-    const size_t tiles = size_t((c->p.Lx + kTbTile - 1) / kTbTile) * ((c->p.Ly + kTbTile - 1) / kTbTile);
-    const int tgrid = int(std::min<size_t>(tiles, size_t(c->sms) * 2));
+    const int tgrid = tb_grid(c);
     for (uint32_t k = 0; k + tb <= T; k += tb) {
       cudaError_t e = launch_step_tb(a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), tb, kTbTile, c->d_fail, tgrid,
                                      c->stream);
@@ -382,11 +418,7 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
     }
   }
   while (t < t0 + T) {
-    cudaError_t e = c->Q == 9 ? launch_step9(a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid, c->stream)
-                    : vec     ? launch_step_vec(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid,
-                                                c->stream)
-                              : launch_step(c->Q, a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), c->d_fail, grid,
-                                            c->stream);
+    cudaError_t e = launch_single(c, kind, a, c->buf[cur], c->buf[cur ^ 1], t, c->d_fail);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
     launch_t.push_back(t);
     t += 1;
@@ -410,6 +442,110 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   }
   c->cur = cur;
   c->t = t0 + T;
+  return ILG_OK;
+}
+
+ilg_status ilg_set_step_kernel(ilg_ctx* c, int32_t candidate) {
+  if (!c) return ILG_E_INVALID;
+  if (candidate < -1 || candidate > kKernelNode) return fail(c, ILG_E_INVALID, "candidate must be -1, 0, 1 or 2");
+  c->kernel_choice = candidate;
+  return ILG_OK;
+}
+
+ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
+  if (!c) return ILG_E_INVALID;
+  if (!c->has_state) return fail(c, ILG_E_STATE, "no state: call ilg_init or ilg_set_state first");
+  if (trial_steps == 0) trial_steps = 20;
+  if (trial_steps > 1000) return fail(c, ILG_E_INVALID, "at most 1000 trial steps");
+  if (c->t + 2ull * trial_steps + 16 >= (uint64_t(1) << 32))
+    return fail(c, ILG_E_INVALID, "step counter would reach 2^32 in the trials");
+  const StepArgs a = step_args(c);
+  // trials on a copy of the state (two scratch buffers and their own overflow word);
+  // every candidate gives the same bits, only the time is kept
+  const size_t bytes = sizeof(uint16_t) * c->nodes * c->Q;
+  uint16_t* s[2] = {nullptr, nullptr};
+  unsigned long long* fw = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&]() {
+    cudaFree(s[0]);
+    cudaFree(s[1]);
+    cudaFree(fw);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  cudaError_t e = cudaMalloc(&s[0], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s[1], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&fw, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s[0], c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "autotune scratch");
+  }
+  // candidates: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, 3 / 4 temporal
+  // blocking of depth 2 / 4 (D2Q5)
+  ilg_tuning res{};
+  res.n = 5;
+  for (int k = 0; k < 8; ++k) res.ms_per_step[k] = -1.0;
+  auto trial = [&](int cand, double* ms_per_step) -> cudaError_t {
+    const uint32_t depth = cand == 3 ? 2u : (cand == 4 ? 4u : 1u);
+    const uint32_t launches = std::max<uint32_t>(1, trial_steps / depth);
+    uint64_t t = c->t;
+    int cur = 0;
+    auto one = [&]() -> cudaError_t {
+      cudaError_t r = depth > 1 ? launch_step_tb(a, s[cur], s[cur ^ 1], uint32_t(t), depth, kTbTile, fw, tb_grid(c),
+                                                 c->stream)
+                                : launch_single(c, cand, a, s[cur], s[cur ^ 1], t, fw);
+      t += depth;
+      cur ^= 1;
+      return r;
+    };
+    cudaError_t r = cudaMemsetAsync(fw, 0xFF, sizeof(unsigned long long), c->stream);
+    if (r == cudaSuccess) r = one();  // warm-up launch
+    if (r == cudaSuccess) r = cudaEventRecord(e0, c->stream);
+    for (uint32_t k = 0; k < launches && r == cudaSuccess; ++k) r = one();
+    if (r == cudaSuccess) r = cudaEventRecord(e1, c->stream);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(c->h_word, fw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
+    float ms = 0.f;
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+    // a trial that overflowed skipped work after the overflow: its time is not kept
+    if (r == cudaSuccess && *c->h_word == ~0ull) *ms_per_step = double(ms) / (double(launches) * depth);
+    return r;
+  };
+  for (int cand = 0; cand < 5 && e == cudaSuccess; ++cand) {
+    if (cand <= 2 && !kernel_applies(c, a, cand)) continue;
+    if (cand <= 2 && c->Q == 9 && cand != kKernelNode) continue;
+    if (cand >= 3) {
+      if (c->Q != 5) continue;
+      const uint32_t depth = cand == 3 ? 2u : 4u;
+      if ((e = prepare_step_tb_kernel(kTbTile, depth)) != cudaSuccess) break;
+    }
+    e = trial(cand, &res.ms_per_step[cand]);
+  }
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune trial");
+  int best = -1;
+  for (int k = 0; k < 5; ++k)
+    if (res.ms_per_step[k] >= 0.0 && (best < 0 || res.ms_per_step[k] < res.ms_per_step[best])) best = k;
+  if (best < 0) return fail(c, ILG_E_OVERFLOW, "every trial overflowed: no choice made");
+  if (best >= 3) {
+    // temporal blocking; the remaining single steps take the fastest single-step kernel
+    int single = -1;
+    for (int k = 0; k < 3; ++k)
+      if (res.ms_per_step[k] >= 0.0 && (single < 0 || res.ms_per_step[k] < res.ms_per_step[single])) single = k;
+    c->kernel_choice = single;
+    c->tb_depth = best == 3 ? 2u : 4u;
+    ILG_CUDA(c, prepare_step_tb_kernel(kTbTile, c->tb_depth), "cudaFuncSetAttribute");
+  } else {
+    c->kernel_choice = best;
+    c->tb_depth = 0;
+  }
+  res.choice = uint32_t(best);
+  res.tb_depth = c->tb_depth;
+  res.threads = 256;
+  if (out) *out = res;
   return ILG_OK;
 }
 

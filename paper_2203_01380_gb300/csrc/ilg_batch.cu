@@ -257,8 +257,9 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
 
 }  // namespace
 
-// Rings up to kBatchSmallL nodes run on 256-thread blocks, four per SM; longer
-// rings on one 1024-thread block per SM.
+// Default shape: batches whose rings all have at most kBatchSmallL nodes run on
+// 256-thread blocks, several per SM; others on 1024-thread blocks.  The autotuner
+// (ilg_batch_autotune) may pick 256, 512 or 1024 threads instead.
 constexpr int kBatchThreads = 1024;
 constexpr int kBatchSmallThreads = 256;
 constexpr uint32_t kBatchSmallL = 1024;
@@ -268,24 +269,41 @@ size_t batch_smem_bytes(uint32_t Lmax, int threads) {
          sizeof(uint16_t) * 2 * 3 * size_t(Lmax);
 }
 
-cudaError_t prepare_batch_kernel(uint32_t Lmax) {
-  if (Lmax <= kBatchSmallL)
-    return cudaFuncSetAttribute(batch_d1q3_kernel<kBatchSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(batch_smem_bytes(Lmax, kBatchSmallThreads)));
-  return cudaFuncSetAttribute(batch_d1q3_kernel<kBatchThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(batch_smem_bytes(Lmax, kBatchThreads)));
+uint32_t batch_default_threads(uint32_t Lmax) { return Lmax <= kBatchSmallL ? kBatchSmallThreads : kBatchThreads; }
+
+template <int THREADS>
+static cudaError_t batch_attr(uint32_t Lmax) {
+  return cudaFuncSetAttribute(batch_d1q3_kernel<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(batch_smem_bytes(Lmax, THREADS)));
 }
 
-cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int sms, cudaStream_t s) {
-  if (b.Lmax <= kBatchSmallL) {
-    const int grid = int(b.n < uint32_t(4 * sms) ? b.n : uint32_t(4 * sms));
-    batch_d1q3_kernel<kBatchSmallThreads>
-        <<<grid, kBatchSmallThreads, batch_smem_bytes(b.Lmax, kBatchSmallThreads), s>>>(b, common);
-  } else {
-    const int grid = int(b.n < uint32_t(sms) ? b.n : uint32_t(sms));
-    batch_d1q3_kernel<kBatchThreads><<<grid, kBatchThreads, batch_smem_bytes(b.Lmax, kBatchThreads), s>>>(b, common);
-  }
+cudaError_t prepare_batch_kernel(uint32_t Lmax, int threads) {
+  if (threads == 256) return batch_attr<256>(Lmax);
+  if (threads == 512) return batch_attr<512>(Lmax);
+  if (threads == 1024) return batch_attr<1024>(Lmax);
+  return cudaErrorInvalidValue;
+}
+
+// Persistent grid: as many blocks as fit on every SM (shared memory and registers
+// decide), at most one per ring.
+template <int THREADS>
+static cudaError_t launch_shape(const BatchArgs& b, const StepArgs& common, int sms, cudaStream_t s) {
+  const size_t smem = batch_smem_bytes(b.Lmax, THREADS);
+  int per_sm = 1;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_d1q3_kernel<THREADS>, THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const uint32_t cap = uint32_t(per_sm) * uint32_t(sms);
+  const int grid = int(b.n < cap ? b.n : cap);
+  batch_d1q3_kernel<THREADS><<<grid, THREADS, smem, s>>>(b, common);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int sms, cudaStream_t s, int threads) {
+  if (threads == 0) threads = int(batch_default_threads(b.Lmax));
+  if (threads == 256) return launch_shape<256>(b, common, sms, s);
+  if (threads == 512) return launch_shape<512>(b, common, sms, s);
+  return launch_shape<1024>(b, common, sms, s);
 }
 
 }  // namespace ilg

@@ -44,8 +44,11 @@ struct BatchArgs {
 };
 
 size_t batch_smem_bytes(uint32_t Lmax, int threads);
-cudaError_t prepare_batch_kernel(uint32_t Lmax);
-cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int sms, cudaStream_t s);
+// block shapes: 256, 512 or 1024 threads (ceil(L / threads) nodes per thread and step)
+uint32_t batch_default_threads(uint32_t Lmax);
+cudaError_t prepare_batch_kernel(uint32_t Lmax, int threads);
+// threads 0: the default shape for Lmax
+cudaError_t launch_batch(const BatchArgs& b, const StepArgs& common, int sms, cudaStream_t s, int threads = 0);
 cudaError_t launch_batch_obs(const ReplicaDesc* desc, const uint16_t* state, uint32_t n, int32_t mode,
                              unsigned long long* mass, double* amp, cudaStream_t s);
 cudaError_t launch_batch_amp(const ReplicaDesc* desc, const double* record, uint32_t n, uint32_t T, double* amp,

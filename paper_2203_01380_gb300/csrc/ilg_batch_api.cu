@@ -24,6 +24,7 @@ struct ilg_batch {
   bool own_stream = false;            // created here: a capture needs a non-legacy stream
   int sms = 0;
   uint32_t Lmax = 0;
+  int threads = 0;                    // block shape of the batch kernel (default or autotuned)
   size_t total = 0;                   // uint16 words of state
   uint16_t* d_state = nullptr;
   ReplicaDesc* d_desc = nullptr;
@@ -171,7 +172,8 @@ ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, 
       (e = cudaMemsetAsync(b->d_state, 0, sizeof(uint16_t) * b->total, b->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
     return bail(e, "upload");
-  if ((e = prepare_batch_kernel(b->Lmax)) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
+  b->threads = int(batch_default_threads(b->Lmax));
+  if ((e = prepare_batch_kernel(b->Lmax, b->threads)) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   round_keys(params[0].seed, b->common.rk);
   b->common.key0 = uint32_t(params[0].seed);
   b->common.key1 = uint32_t(params[0].seed >> 32);
@@ -317,7 +319,7 @@ ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec,
     BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_failed, 0, sizeof(uint32_t) * b->n, b->stream);
-    if (e == cudaSuccess) e = launch_batch(a, b->common, b->sms, b->stream);
+    if (e == cudaSuccess) e = launch_batch(a, b->common, b->sms, b->stream, b->threads);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -411,6 +413,94 @@ ilg_status ilg_batch_ensemble(ilg_batch* b, uint32_t T, int32_t mode, double* st
                              b->stream),
           "read record");
   return batch_finish(b, failed);
+}
+
+ilg_status ilg_batch_autotune(ilg_batch* b, uint32_t trial_steps, ilg_tuning* out) {
+  if (!b) return ILG_E_INVALID;
+  if (trial_steps == 0) trial_steps = 50;
+  if (trial_steps > 10000) return bfail(b, ILG_E_INVALID, "at most 10000 trial steps");
+  for (const auto& d : b->desc)
+    if (uint64_t(d.t) + 8ull * trial_steps >= (uint64_t(1) << 32))
+      return bfail(b, ILG_E_INVALID, "step counter would reach 2^32 in the trials");
+  // the trials run on copies of the rings and descriptors; results are discarded
+  uint16_t* s_state = nullptr;
+  ReplicaDesc* s_desc = nullptr;
+  unsigned int* s_counter = nullptr;
+  uint32_t* s_failed = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&]() {
+    cudaFree(s_state);
+    cudaFree(s_desc);
+    cudaFree(s_counter);
+    cudaFree(s_failed);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  cudaError_t e = cudaMalloc(&s_state, sizeof(uint16_t) * b->total);
+  if (e == cudaSuccess) e = cudaMalloc(&s_desc, sizeof(ReplicaDesc) * b->n);
+  if (e == cudaSuccess) e = cudaMalloc(&s_counter, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&s_failed, sizeof(uint32_t) * b->n);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s_state, b->d_state, sizeof(uint16_t) * b->total, cudaMemcpyDeviceToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s_desc, b->d_desc, sizeof(ReplicaDesc) * b->n, cudaMemcpyDeviceToDevice, b->stream);
+  if (e != cudaSuccess) {
+    release();
+    return bcuda(b, e, "autotune scratch");
+  }
+  static const int kShapes[3] = {256, 512, 1024};
+  ilg_tuning res{};
+  res.n = 3;
+  for (int k = 0; k < 8; ++k) res.ms_per_step[k] = -1.0;
+  int best = -1;
+  for (int k = 0; k < 3; ++k) {
+    const int threads = kShapes[k];
+    if (prepare_batch_kernel(b->Lmax, threads) != cudaSuccess) {  // the rings do not fit this shape
+      cudaGetLastError();
+      continue;
+    }
+    BatchArgs a{};
+    a.n = b->n;
+    a.T = trial_steps;
+    a.Lmax = b->Lmax;
+    a.order = b->d_order;
+    a.desc = s_desc;
+    a.tables = b->d_tables;
+    a.state = s_state;
+    a.counter = s_counter;
+    a.failed = s_failed;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+      e = cudaMemsetAsync(s_counter, 0, sizeof(unsigned int), b->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(s_failed, 0, sizeof(uint32_t) * b->n, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      if (e == cudaSuccess) e = launch_batch(a, b->common, b->sms, b->stream, threads);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e != cudaSuccess) {
+      release();
+      prepare_batch_kernel(b->Lmax, b->threads);
+      return bcuda(b, e, "autotune trial");
+    }
+    res.ms_per_step[k] = double(ms) / trial_steps;
+    if (best < 0 || res.ms_per_step[k] < res.ms_per_step[best]) best = k;
+  }
+  release();
+  if (best < 0) return bfail(b, ILG_E_INVALID, "no block shape fits the rings");
+  b->threads = kShapes[best];
+  BCUDA(b, prepare_batch_kernel(b->Lmax, b->threads), "cudaFuncSetAttribute");
+  if (b->graph) {  // the next run captures the chosen shape
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  res.choice = uint32_t(best);
+  res.threads = uint32_t(b->threads);
+  if (out) *out = res;
+  return ILG_OK;
 }
 
 ilg_status ilg_batch_observables(ilg_batch* b, int32_t mode, uint64_t* mass, double* amp) {

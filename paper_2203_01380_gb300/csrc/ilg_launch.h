@@ -26,9 +26,11 @@ cudaError_t prepare_step_kernels();  // opt in to the table block's shared memor
 cudaError_t launch_step(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                         unsigned long long* fail, int grid, cudaStream_t s);
 cudaError_t prepare_step_vec_kernels();
-uint32_t step_vec_width();  // nodes per thread of the row-tiled step (rows must be a multiple)
+uint32_t step_vec_width();  // nodes per thread of the default row-tiled step (rows must be a multiple)
+uint32_t step_vec_blocks_per_sm(int npt);
+// npt: nodes per thread, 8 (default) or 4 (rows a multiple of npt)
 cudaError_t launch_step_vec(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
-                            unsigned long long* fail, int grid, cudaStream_t s);
+                            unsigned long long* fail, int grid, cudaStream_t s, int npt = 8);
 size_t step_tb_smem_bytes(uint32_t B, uint32_t Tb);
 cudaError_t prepare_step_tb_kernel(uint32_t B, uint32_t Tb);
 cudaError_t launch_step_tb(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t0, uint32_t Tb,

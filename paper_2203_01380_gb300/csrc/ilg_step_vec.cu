@@ -272,19 +272,36 @@ constexpr int kNPT = 8;
 constexpr bool kUnroll = true;
 constexpr int kMinBlocks = 3;
 
+// second shape for the autotuner: 4 nodes per thread, 4 blocks per SM
+constexpr int kNPT4 = 4;
+constexpr int kMinBlocks4 = 4;
+
+template <int Q, int NPT, int MINB>
+static cudaError_t vec_attr() {
+  return cudaFuncSetAttribute(step_vec_kernel<Q, NPT, kUnroll, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(kVecSmem));
+}
+
 cudaError_t prepare_step_vec_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(step_vec_kernel<3, kNPT, kUnroll, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(kVecSmem));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(step_vec_kernel<5, kNPT, kUnroll, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kVecSmem));
+  cudaError_t e = vec_attr<3, kNPT, kMinBlocks>();
+  if (e == cudaSuccess) e = vec_attr<5, kNPT, kMinBlocks>();
+  if (e == cudaSuccess) e = vec_attr<3, kNPT4, kMinBlocks4>();
+  if (e == cudaSuccess) e = vec_attr<5, kNPT4, kMinBlocks4>();
+  return e;
 }
 
 uint32_t step_vec_width() { return kNPT; }
+uint32_t step_vec_blocks_per_sm(int npt) { return npt == kNPT4 ? kMinBlocks4 : kMinBlocks; }
 
 cudaError_t launch_step_vec(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
-                            unsigned long long* fail, int grid, cudaStream_t s) {
-  if (Q == 3) step_vec_kernel<3, kNPT, kUnroll, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
-  else step_vec_kernel<5, kNPT, kUnroll, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+                            unsigned long long* fail, int grid, cudaStream_t s, int npt) {
+  if (npt == kNPT4) {
+    if (Q == 3) step_vec_kernel<3, kNPT4, kUnroll, kMinBlocks4><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+    else step_vec_kernel<5, kNPT4, kUnroll, kMinBlocks4><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+  } else {
+    if (Q == 3) step_vec_kernel<3, kNPT, kUnroll, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+    else step_vec_kernel<5, kNPT, kUnroll, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+  }
   return cudaGetLastError();
 }
 
