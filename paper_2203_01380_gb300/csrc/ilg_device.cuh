@@ -169,117 +169,94 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* s, ui
   }
 }
 
-// Extension words held in shared memory: this thread's buffer holds words
-// [base, base + K) of its extension stream, word e at xb[(e - base) * S] (threads
-// interleaved with stride S, so a warp's accesses hit distinct banks).  Blocks are
-// generated in order, a phase at a time; a word past the buffer refills it with
-// the next K words.  Same stream, same bits as the lazy reader.
-template <int K, int S>
-struct ExtBuffer {
+// The general collision of one node (any occupations), in the same word order as
+// collide(): the extension words [0, K) of the node are generated before the
+// phase that first needs them (thinning chunks, then rest chunks, then moving
+// groups), a whole Philox block at a time, into this thread's shared-memory
+// buffer (word e at xb[e * S]; threads interleaved with stride S, so a warp's
+// accesses hit distinct banks), so a warp runs its blocks together; words beyond K
+// are read lazily.  A probability of 0 or 2^32 draws nothing.
+template <int Q, int K, int S>
+__device__ __forceinline__ void collide_buffered(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
+                                                 const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
   static_assert(K % 4 == 0, "whole Philox blocks");
-  uint32_t* xb;
-  uint32_t base;    // first word held (a multiple of 4)
-  uint32_t filled;  // words generated so far (base <= filled <= base + K)
-  uint32_t next;    // words consumed so far
-
-  __device__ __forceinline__ void fill(const StepArgs& a, uint32_t node, uint32_t t, uint32_t upto) {
-    upto = upto < base + uint32_t(K) ? upto : base + uint32_t(K);
-    while (filled < upto) {
+  const uint2* to = thinning_table(s);
+  const uint2* tr = rest_table(s);
+  auto extra = [](uint32_t mode, uint32_t x) -> uint32_t { return mode == kTable && x > kDevNmax ? (x - 1) >> 6 : 0u; };
+  uint32_t need = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) need += extra(a.omega_mode, m[i]);
+  const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
+  const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
+  const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  uint32_t filled = 0;
+  auto gen = [&](uint32_t upto) {
+    upto = upto < uint32_t(K) ? upto : uint32_t(K);
+    for (; filled < upto; filled += 4) {
       const uint4 b = philox_rk(make_uint4(node, t, a.replica, kDevTagExt | (filled >> 2)), a.rk);
-      uint32_t* p = xb + (filled - base) * S;
+      uint32_t* p = xb + filled * S;
       p[0] = b.x;
       p[S] = b.y;
       p[2 * S] = b.z;
       p[3 * S] = b.w;
-      filled += 4;
     }
-  }
-  __device__ __forceinline__ uint32_t take(const StepArgs& a, uint32_t node, uint32_t t) {
-    const uint32_t e = next++;
-    if (e >= filled) {
-      if (e >= base + uint32_t(K)) {
-        base = e & ~3u;
-        filled = base;
-      }
-      fill(a, node, t, base + uint32_t(K));
-    }
-    return xb[(e - base) * S];
-  }
-};
-
-// Binomial(m, P) with the chunks beyond the first drawn from the buffer.
-template <int K, int S>
-__device__ __forceinline__ uint32_t binomial_buf(uint32_t mode, const uint2* A, uint32_t m, uint32_t slot,
-                                                 const StepArgs& a, uint32_t node, uint32_t t,
-                                                 ExtBuffer<K, S>& eb) {
-  if (mode == kNever || m == 0) return 0;
-  if (mode == kAlways) return m;
-  uint32_t r = binomial_alias(A, m < kDevNmax ? m : kDevNmax, slot);
-  for (uint32_t left = m > kDevNmax ? m - kDevNmax : 0; left > 0;) {
-    const uint32_t c = left < kDevNmax ? left : kDevNmax;
-    r += binomial_alias(A, c, eb.take(a, node, t));
-    left -= c;
-  }
-  return r;
-}
-
-__device__ __forceinline__ uint32_t extra_chunks(uint32_t mode, uint32_t m) {
-  return (mode == kTable && m > kDevNmax) ? (m - 1) / kDevNmax : 0u;
-}
-
-// The general collision, phase by phase: the extension words each phase needs
-// (thinning chunks, rest chunks, moving groups) are generated together, once,
-// before the phase, so a warp runs the Philox blocks in one place.  Same words,
-// same order and same result as collide().
-template <int Q, int K, int S>
-__device__ __forceinline__ void collide_phased(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
-                                               const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
-  const uint2* to = thinning_table(s);
-  const uint2* tr = rest_table(s);
-  const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
-  const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
-  const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-  ExtBuffer<K, S> eb{xb, 0u, 0u, 0u};
-
-  uint32_t need = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) need += extra_chunks(a.omega_mode, m[i]);
-  eb.fill(a, node, t, need);
+  };
+  ExtStream lazy{node, t, 0u, 0xFFFFFFFFu, make_uint4(0, 0, 0, 0)};
+  auto word = [&](uint32_t e) -> uint32_t {
+    if (e < uint32_t(K)) return xb[e * S];
+    lazy.next = e;
+    return ext_word(a, lazy);
+  };
+  uint32_t e = 0;
+  // Binomial(x, P) in chunks of 64 trials: the first with the slot word, the others
+  // with the next extension words
+  auto draw = [&](uint32_t mode, const uint2* A, uint32_t x, uint32_t slot) -> uint32_t {
+    if (mode == kNever) return 0u;
+    if (mode == kAlways) return x;
+    uint32_t r = binomial_alias(A, x < kDevNmax ? x : kDevNmax, slot);
+    for (uint32_t left = x > kDevNmax ? x - kDevNmax : 0u; left > 0; left -= (left < kDevNmax ? left : kDevNmax))
+      r += binomial_alias(A, left < kDevNmax ? left : kDevNmax, word(e++));
+    return r;
+  };
+  gen(need);
   uint32_t removed = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const uint32_t r = binomial_buf<K, S>(a.omega_mode, to, m[i], W[i], a, node, t, eb);
+    const uint32_t r = draw(a.omega_mode, to, m[i], W[i]);
     out[i] = m[i] - r;
     removed += r;
   }
-  need += extra_chunks(a.rest_mode, removed);
-  eb.fill(a, node, t, need);
-  const uint32_t to_rest = binomial_buf<K, S>(a.rest_mode, tr, removed, W[Q], a, node, t, eb);
+  need += extra(a.rest_mode, removed);
+  gen(need);
+  const uint32_t to_rest = draw(a.rest_mode, tr, removed, W[Q]);
   out[0] += to_rest;
-  uint32_t moving = removed - to_rest;
-  const uint32_t groups = (moving + 31) / 32;
-  need += (groups > 1 ? groups - 1 : 0) * (Q == 5 ? 2u : 1u);
-  eb.fill(a, node, t, need);
-  bool first = true;
-  while (moving > 0) {
-    const uint32_t c = moving < 32 ? moving : 32;
-    const uint32_t mask = c == 32 ? 0xFFFFFFFFu : ((1u << c) - 1u);
+  const uint32_t moving = removed - to_rest;
+  const uint32_t groups = (moving + 31) >> 5;
+  need += groups > 1 ? (groups - 1) * (Q == 5 ? 2u : 1u) : 0u;
+  gen(need);
+  // groups of 32 moving particles: D1Q3 one sign word, D2Q5 an axis and a sign word
+  uint32_t left = moving;
+  uint32_t A = W[Q + 1], Bw = Q == 5 ? W[Q + 2] : 0u;
+  while (left > 0) {
+    const uint32_t c = left < 32 ? left : 32;
+    const uint32_t mask = __funnelshift_lc(0xFFFFFFFFu, 0u, c);
     if constexpr (Q == 3) {
-      const uint32_t sw = first ? W[Q + 1] : eb.take(a, node, t);
-      const uint32_t minus = __popc(sw & mask);
+      const uint32_t minus = __popc(A & mask);
       out[1] += c - minus;
       out[2] += minus;
     } else {
-      const uint32_t ax = (first ? W[Q + 1] : eb.take(a, node, t)) & mask;
-      const uint32_t sg = (first ? W[Q + 2] : eb.take(a, node, t)) & mask;
+      const uint32_t ax = A & mask, sg = Bw & mask;
       const uint32_t ny = __popc(ax), nmy = __popc(ax & sg), nmx = __popc(sg & ~ax);
       out[1] += c - ny - nmx;
       out[2] += nmx;
       out[3] += ny - nmy;
       out[4] += nmy;
     }
-    moving -= c;
-    first = false;
+    left -= c;
+    if (left > 0) {
+      A = word(e++);
+      if constexpr (Q == 5) Bw = word(e++);
+    }
   }
 }
 
@@ -344,7 +321,7 @@ template <int Q, int K, int S>
 __device__ __forceinline__ void collide_general(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
                                                 const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
   if (a.particle) collide_particle<Q>(a, s, node, t, m, out);
-  else collide_phased<Q, K, S>(a, s, node, t, m, out, xb);
+  else collide_buffered<Q, K, S>(a, s, node, t, m, out, xb);
 }
 
 // The collision of one node, fast path: every occupation <= 63, at most 63
