@@ -194,12 +194,12 @@ def alu_roofline(nodes, launch_ms, clocks, choice="vec8"):
             "ops_per_node_update": OPS_PER_NU, "peak_clock_mhz": mhz}
 
 
-def measure_batched(torch, B, dev):
+def measure_batched(torch, B, dev, rings=4096, T=5000):
     """4096 D1Q3 rings, 5000 steps in one persistent launch, against one context per
-    ring on a sample of 16 rings (500 steps each) at identical results."""
-    reps = inputs.batch_replicas()
+    ring on a sample of 16 rings (500 steps each) at identical results.  Fewer rings or
+    steps only for profiling captures."""
+    reps = inputs.batch_replicas(rings)
     nodes = sum(r["Lx"] for r in reps)
-    T = 5000
     st = torch.cuda.Stream(dev)
     with B.Batch(reps, stream=st) as bat:
         bat.init()
@@ -222,8 +222,8 @@ def measure_batched(torch, B, dev):
     plain_s = time.perf_counter() - t0
     v = nodes * T / (ms / 1e3) / 1e9
     vp = pn / plain_s / 1e9
-    return {"workload": "batch_d1q3: 4096 rings, L log-uniform [64, 8192], n0 uniform [5, 200], "
-                        "omega_eff uniform [0.2, 1.95], 5000 steps, one persistent graph-captured launch",
+    return {"workload": f"batch_d1q3: {rings} rings, L log-uniform [64, 8192], n0 uniform [5, 200], "
+                        f"omega_eff uniform [0.2, 1.95], {T} steps, one persistent graph-captured launch",
             "value": v, "unit": "GNUPS", "ms": ms, "node_updates": nodes * T,
             "plain_per_ring_launch": {"value": vp, "unit": "GNUPS",
                                       "sample": "16 rings (evenly spaced in the list), init + 500 steps each, one context each, host wall clock"},
@@ -464,6 +464,9 @@ def main():
     ap.add_argument("--extra", default="tb,batched,lb,ensemble,particle,d2q9,serving",
                     help="comma-separated measurements beyond the main workload")
     ap.add_argument("--lb-side", type=int, default=0, help="side of the lattice Boltzmann workload (default 16384)")
+    ap.add_argument("--batch-rings", type=int, default=4096, help="rings of the batched workload (profiling only)")
+    ap.add_argument("--batch-steps", type=int, default=5000, help="steps of the batched workload (profiling only)")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests of the serving workload (profiling only)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     cfg = {k: v for k, v in inputs.LARGE_D2Q5.items() if k != "steps"}
@@ -567,7 +570,7 @@ def main():
             extra["temporal_blocking"] = {"steps_per_launch": tb, "single_step_kernel": {"value": value, "unit": "GNUPS"},
                                           "tile": "48 x 48 with a halo of depth nodes"}
         if "batched" in parts:
-            extra["batched"] = measure_batched(torch, B, dev)
+            extra["batched"] = measure_batched(torch, B, dev, args.batch_rings, args.batch_steps)
         if "lb" in parts:
             extra["lattice_boltzmann"] = measure_lb(torch, B, dev, clk.summary(), args.lb_side)
         if "ensemble" in parts:
@@ -577,7 +580,7 @@ def main():
         if "d2q9" in parts:
             extra["d2q9"] = measure_d2q9(torch, B, dev, args.side)
         if "serving" in parts:
-            extra["serving"] = measure_serving(B)
+            extra["serving"] = measure_serving(B, args.serve_requests)
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:

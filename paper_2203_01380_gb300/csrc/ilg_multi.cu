@@ -58,7 +58,7 @@ __device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s,
 }
 
 template <int Q>
-__global__ void __launch_bounds__(kMultiThreads, 3) multi_step_kernel(MultiArgs ma, StepArgs common,
+__global__ void __launch_bounds__(kMultiThreads, kMultiBlocksPerSm) multi_step_kernel(MultiArgs ma, StepArgs common,
                                                                       uint32_t sub) {
   extern __shared__ uint4 smem4[];
   uint32_t* s = reinterpret_cast<uint32_t*>(smem4);

@@ -376,7 +376,8 @@ void worker_main(ilg_server* s) {
       ma.n_items = uint32_t(items.size());
       ma.counter = s->d_counters;
       ma.fail = s->d_fail;
-      const int grid = int(std::min<size_t>(items.size(), size_t(s->sms) * 4));
+      // persistent blocks: as many as are resident at once (3 per SM at this register count)
+      const int grid = int(std::min<size_t>(items.size(), size_t(s->sms) * kMultiBlocksPerSm));
       for (uint32_t sub = 0; sub < q && e == cudaSuccess; ++sub) e = launch_multi_step(ma, s->common, sub, grid, s->stream);
       std::vector<uint32_t> fail(lat.size());
       if (e == cudaSuccess)
