@@ -41,10 +41,10 @@ BYTES_PER_NU = 20  # read + write of 5 uint16 occupations
 OPS_PER_NU = 209
 INT_LANES_PER_SM_CYCLE = 128
 SMS = 152
-# DRAM bytes (read + write) of one 16384^2 launch of the step kernel, from the ncu
-# capture summarised in profiles/ (scaled from a 4096^2 launch by node count); None
-# when the kernel changed after the capture
-TRAFFIC_BYTES_PER_LAUNCH = 4.611e9
+# DRAM bytes (read + write) of one 16384^2 launch of a step kernel, from the ncu
+# capture summarised in profiles/ (scaled from a 4096^2 launch by node count); only
+# kernels unchanged since their capture are listed
+TRAFFIC_BYTES_PER_LAUNCH = {}
 
 
 def peaks():
@@ -178,10 +178,10 @@ def oracle_all_cores(cfg, side, steps, seconds):
 
 
 KERNEL_NAMES = {"vec8": "step_vec_kernel<5, 8>", "vec4": "step_vec_kernel<5, 4>", "node": "step_kernel<5>",
-                "tb2": "step_tb_kernel (depth 2)", "tb4": "step_tb_kernel (depth 4)"}
+                "tb2": "step_tb_kernel (depth 2)", "tb4": "step_tb_kernel (depth 4)", "seg8": "step_seg_kernel<5, 8>"}
 
 
-def alu_roofline(nodes, launch_ms, clocks, choice="vec8"):
+def alu_roofline(nodes, launch_ms, clocks, choice="seg8"):
     """The step kernel is bound by integer issue: OPS_PER_NU algorithmic int32
     operations per node update against 128 int32 lane-operations per SM per cycle
     at the SM clock measured during the run."""
@@ -189,7 +189,7 @@ def alu_roofline(nodes, launch_ms, clocks, choice="vec8"):
     peak = INT_LANES_PER_SM_CYCLE * SMS * mhz * 1e6 / 1e9          # Gop/s
     achieved = OPS_PER_NU * nodes / (launch_ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_BYTES_PER_LAUNCH if choice == "vec8" else None,
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(choice),
             "kernel": KERNEL_NAMES.get(choice, choice), "launch_ms": launch_ms,
             "ops_per_node_update": OPS_PER_NU, "peak_clock_mhz": mhz}
 

@@ -3,11 +3,13 @@
  * over-relaxed diffusive integer lattice gas of Strand & Wagner,
  * "Over-Relaxation in Diffusive Integer Lattice Gas" (arXiv 2203.01380).
  *
- * One time step, for every node x of a periodic D1Q3 or D2Q5 lattice:
+ * One time step, for every node x of a periodic D1Q3, D2Q5 or D2Q9 lattice:
  *   flip      m_i = n_{-i}(x,t) when omega_eff > 1            (Sec. III, Eq. flip)
  *   collide   sampling collision with fraction omega*:         (Sec. II; Sec. III, Eq. LGflip)
  *             binomial thinning, multinomial redistribution
  *             with weights w_i; mass conserved exactly         (Sec. II, Eq. 2)
+ *             (D2Q9, the paper's D1Q3 extended to the product
+ *             lattice: see theta below)
  *   stream    n_i(x + v_i, t+1) = n'_i(x)                      (Sec. II, Eq. ilgeq)
  * with omega^j = 2 - omega* above omega_eff = 1                 (Sec. IV, Eq. omegaj).
  *
@@ -129,8 +131,9 @@ ilg_status ilg_get_state_device(ilg_ctx* ctx, uint16_t* dev, size_t n, uint64_t*
 ilg_status ilg_step(ilg_ctx* ctx, uint32_t T);
 
 /* Temporal blocking (D2Q5): with depth >= 2, ilg_step runs blocks of `depth` steps
- * per launch (48 x 48 tiles with a halo of depth nodes, recomputed, held in shared
- * memory) and single steps for the remainder; results are bit-identical to single
+ * per launch (square tiles of 44 - 2 depth nodes with a halo of depth nodes,
+ * recomputed, held in shared memory) and single steps for the remainder; results
+ * are bit-identical to single
  * steps.  depth 0 or 1 switches it off (the default); at most 8.  On
  * ILG_E_OVERFLOW the state is the input of the failing launch. */
 ilg_status ilg_set_temporal_blocking(ilg_ctx* ctx, uint32_t depth);
@@ -139,10 +142,13 @@ ilg_status ilg_set_temporal_blocking(ilg_ctx* ctx, uint32_t depth);
  * current state (2 extra state buffers, freed before return) and keeps the fastest
  * for later ilg_step calls:
  *   candidate 0  row-tiled step, 8 nodes per thread (16-byte vectors), 3 blocks per SM
- *   candidate 1  row-tiled step, 4 nodes per thread (8-byte vectors), 4 blocks per SM
+ *   candidate 1  row-tiled step, 4 nodes per thread (8-byte vectors), 3 blocks per SM
  *   candidate 2  node-parallel step, one node per thread
  *   candidate 3, 4  temporal blocking of depth 2, 4 (D2Q5; the remainder of a call
- *                takes the fastest of 0-2)
+ *                takes the fastest single-step candidate)
+ *   candidate 5  8-node vectors in warp segments: each warp walks 8192 nodes of a row,
+ *                neighbours exchanged by shuffles, no block barrier (the default
+ *                where the lattice has two segments per resident warp)
  * Candidates that do not apply (row length, D2Q9, occupations that need the general
  * collision) are skipped (ms_per_step < 0).  A choice that stops applying after
  * ilg_set_state (e.g. occupations rise) falls back to the default.  trial_steps:
@@ -158,7 +164,7 @@ typedef struct {
 } ilg_tuning;
 
 ilg_status ilg_autotune(ilg_ctx* ctx, uint32_t trial_steps, ilg_tuning* out);
-/* Set the single-step kernel by hand: candidate 0, 1 or 2 as above, -1 the default.
+/* Set the single-step kernel by hand: candidate 0, 1, 2 or 5 as above, -1 the default.
  * A candidate that does not apply to the current state falls back to the default;
  * results are the same bits either way. */
 ilg_status ilg_set_step_kernel(ilg_ctx* ctx, int32_t candidate);
@@ -359,13 +365,13 @@ ilg_status ilg_observables_noalloc(int32_t lattice, uint32_t Lx, uint32_t Ly, co
 /* Diagnostics of the building blocks, for parity tests.
  * ilg_philox: n Philox4x32-10 blocks computed on the device; ctr (4n words) and out
  *   (4n words) are host arrays; key = (seed lo32, seed hi32).
- * ilg_binomial_table: the 2080-entry integer CDF table (rows n = 1..64, row n at
+ * ilg_binomial_table: the 2016-entry integer CDF table (rows n = 1..63, row n at
  *   offset n(n-1)/2) of Binomial(n, P / 2^32), 0 < P < 2^32; host only.
- * ilg_alias_table: the 2145-entry alias tables (rows n = 0..64, row n at offset
- *   n(n+1)/2, column j of row n at offset n(n+1)/2 + j) the collision draws
- *   Binomial(n, P / 2^32) with: a draw u takes column j = floor(u (n+1) / 2^32) and
- *   yields j if u < thr[.], else alias[.]; they realise the CDF table's integer pmf
- *   exactly.  Host only.
+ * ilg_alias_table: the 4096-entry alias tables (rows n = 0..63 of 64 columns, column
+ *   j of row n at offset 64 n + j) the collision draws Binomial(n, P / 2^32) with: a
+ *   draw u takes column j = u >> 26 and yields j if u < thr[.], else alias[.]; they
+ *   realise the CDF table's integer pmf exactly (outcomes above n get no draw).
+ *   Host only.
  * ilg_poisson_table: the Poisson CDF table of the initial state for mean lambda;
  *   writes at most cap entries and their count to *K; host only. */
 ilg_status ilg_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t n, void* stream);

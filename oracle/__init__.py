@@ -33,7 +33,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ilg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-NMAX = 64
+NMAX = 63          # largest trial count of one alias-table row (chunks of 63 trials)
+ALIAS_COLS = 64    # columns per alias row: a draw u takes column u >> 26
 POISSON_KMAX = 4096
 D1Q3, D2Q5, D2Q9 = 1, 2, 3
 TWO32 = 1 << 32
@@ -159,13 +160,15 @@ def binomial_table(P: int, nmax: int = NMAX) -> np.ndarray:
     return T
 
 
-ALIAS_ENTRIES = (NMAX + 1) * (NMAX + 2) // 2   # rows n = 0..NMAX, n + 1 columns each
+ALIAS_ENTRIES = (NMAX + 1) * ALIAS_COLS   # rows n = 0..NMAX, 64 columns each
 
 
 def alias_table(P: int, nmax: int = NMAX):
-    """(thr, alias) of the alias tables of Binomial(n, P/2^32), n = 0..nmax; row n at
-    offset n(n+1)/2."""
-    n_ent = (nmax + 1) * (nmax + 2) // 2
+    """(thr, alias) of the alias tables of Binomial(n, P/2^32), n = 0..nmax <= 63; row n
+    at offset 64 n, column j of row n covering the draws j 2^26 <= u < (j+1) 2^26."""
+    if not 0 <= nmax < ALIAS_COLS:
+        raise ValueError("alias rows hold at most 64 outcomes")
+    n_ent = (nmax + 1) * ALIAS_COLS
     thr = np.zeros(n_ent, dtype=np.uint32)
     al = np.zeros(n_ent, dtype=np.uint8)
     lib().oracle_alias_table(ctypes.c_uint64(P), nmax, thr, al)

@@ -27,7 +27,7 @@
  *   3. streaming n_i(x + v_i, t+1) = n'_i(x), periodic (Sec. II, Eq. ilgeq).
  *
  * Randomness: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here
- * from its published round function.  Counter = (node id, t, replica,
+ * from its published round function.  Counter = (t, node id, replica,
  * tag<<24 | block), key = (seed lo, seed hi); word d of a stream is lane d&3 of
  * block d>>2.  Binomial draws go through an alias table built in integers from
  * a pmf that is defined by an integer Pascal recurrence (below), so both
@@ -38,7 +38,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OR_NMAX 64u /* largest binomial trial count taken by one table row */
+#define OR_NMAX 63u      /* largest binomial trial count taken by one table row */
+#define OR_ALIAS_COLS 64u /* columns of every alias row; column j covers u >> 26 == j */
 #define OR_TAG_STEP 1u
 #define OR_TAG_EXT 2u
 #define OR_TAG_INIT 3u
@@ -68,10 +69,10 @@ void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* word d of the stream (node, t, replica, tag) under key seed */
+/* word d of the stream (t, node, replica, tag) under key seed */
 static uint32_t stream_word(uint64_t seed, uint32_t node, uint32_t t, uint32_t replica,
                             uint32_t tag, uint32_t d) {
-  uint32_t ctr[4] = {node, t, replica, (tag << 24) | (d >> 2)};
+  uint32_t ctr[4] = {t, node, replica, (tag << 24) | (d >> 2)};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t out[4];
   oracle_philox(ctr, key, out);
@@ -116,40 +117,40 @@ void oracle_binomial_table(uint64_t P, uint32_t nmax, uint32_t *T) {
 
 /*
  * Alias table (Walker's method, Vose's construction in integers) over the same
- * integer pmf.  Row n (0 <= n <= nmax) has n+1 columns j, stored at offset
- * n(n+1)/2.  Outcome weights: W_0 = T[n][0], W_k = T[n][k] - T[n][k-1],
- * W_n = 2^32 - T[n][n-1] (W_0 = 2^32 for n = 0); they sum to 2^32.  Column j
- * covers the draws a_j <= u < a_{j+1}, a_j = ceil(j 2^32 / (n+1)), size s_j.
- * A draw u picks column j = floor(u (n+1) / 2^32) and yields j if u < thr[j],
+ * integer pmf.  Row n (0 <= n <= nmax <= 63) has 64 columns j of 2^26 draws
+ * each (column j covers j 2^26 <= u < (j+1) 2^26), stored at offset 64 n.
+ * Outcome weights: W_0 = T[n][0], W_k = T[n][k] - T[n][k-1] (0 < k < n),
+ * W_n = 2^32 - T[n][n-1] (W_0 = 2^32 for n = 0), W_k = 0 for n < k < 64; they
+ * sum to 2^32.  A draw u picks column j = u >> 26 and yields j if u < thr[j],
  * else alias[j].
- * Construction: columns with W_j = s_j are full (alias = j); the others go on a
- * "small" (W_j < s_j) or "large" (W_j > s_j) stack, pushed in increasing j.
+ * Construction: columns with W_j = 2^26 are full (alias = j); the others go on a
+ * "small" (W_j < 2^26) or "large" (W_j > 2^26) stack, pushed in increasing j.
  * While both stacks are non-empty: pop l (small) and g (large) from their tops;
- * column l gives its first W_l draws to l (thr[l] = a_l + W_l) and the rest to g
- * (alias[l] = g); W_g drops by s_l - W_l and g is pushed back on the stack its
- * new weight belongs to (or is full).  Every outcome's weight is realised exactly.
+ * column l gives its first W_l draws to l (thr[l] = l 2^26 + W_l) and the rest
+ * to g (alias[l] = g); W_g drops by 2^26 - W_l and g is pushed back on the stack
+ * its new weight belongs to (or is full).  Every outcome's weight is realised
+ * exactly; columns of the zero-weight outcomes k > n go wholly to their alias.
  */
 void oracle_alias_table(uint64_t P, uint32_t nmax, uint32_t *thr, uint8_t *alias) {
+  const uint64_t s = (uint64_t)1 << 26; /* draws per column */
+  if (nmax >= OR_ALIAS_COLS) return;     /* a row holds at most 64 outcomes */
   uint32_t *T = (uint32_t *)malloc(sizeof(uint32_t) * (nmax * (nmax + 1) / 2 + 1));
-  uint64_t *W = (uint64_t *)malloc(sizeof(uint64_t) * (nmax + 1));
-  uint32_t *small = (uint32_t *)malloc(sizeof(uint32_t) * (nmax + 1));
-  uint32_t *large = (uint32_t *)malloc(sizeof(uint32_t) * (nmax + 1));
-  uint64_t *a = (uint64_t *)malloc(sizeof(uint64_t) * (nmax + 2));
+  uint64_t W[OR_ALIAS_COLS];
+  uint32_t small[OR_ALIAS_COLS], large[OR_ALIAS_COLS];
   oracle_binomial_table(P, nmax, T);
   for (uint32_t n = 0; n <= nmax; ++n) {
     const uint32_t *row = T + (n ? n * (n - 1) / 2 : 0);
-    uint32_t *th = thr + n * (n + 1) / 2;
-    uint8_t *al = alias + n * (n + 1) / 2;
+    uint32_t *th = thr + OR_ALIAS_COLS * n;
+    uint8_t *al = alias + OR_ALIAS_COLS * n;
     uint64_t prev = 0;
+    for (uint32_t k = 0; k < OR_ALIAS_COLS; ++k) W[k] = 0;
     for (uint32_t k = 0; k < n; ++k) {
       W[k] = (uint64_t)row[k] - prev;
       prev = row[k];
     }
     W[n] = ((uint64_t)1 << 32) - prev;
-    for (uint32_t j = 0; j <= n + 1; ++j) a[j] = (((uint64_t)j << 32) + n) / (n + 1);
     uint32_t ns = 0, nl = 0;
-    for (uint32_t j = 0; j <= n; ++j) {
-      uint64_t s = a[j + 1] - a[j];
+    for (uint32_t j = 0; j < OR_ALIAS_COLS; ++j) {
       th[j] = 0;
       al[j] = (uint8_t)j;
       if (W[j] < s) small[ns++] = j;
@@ -158,22 +159,20 @@ void oracle_alias_table(uint64_t P, uint32_t nmax, uint32_t *thr, uint8_t *alias
     while (ns > 0 && nl > 0) {
       uint32_t l = small[--ns];
       uint32_t g = large[--nl];
-      uint64_t sl = a[l + 1] - a[l];
-      th[l] = (uint32_t)(a[l] + W[l]);
+      th[l] = (uint32_t)((uint64_t)l * s + W[l]);
       al[l] = (uint8_t)g;
-      W[g] -= sl - W[l];
-      uint64_t sg = a[g + 1] - a[g];
-      if (W[g] < sg) small[ns++] = g;
-      else if (W[g] > sg) large[nl++] = g;
+      W[g] -= s - W[l];
+      if (W[g] < s) small[ns++] = g;
+      else if (W[g] > s) large[nl++] = g;
     }
   }
-  free(T); free(W); free(small); free(large); free(a);
+  free(T);
 }
 
 /* Binomial(n, P/2^32) for n <= OR_NMAX: one draw through row n of the alias table */
 static uint32_t binomial_draw(const uint32_t *thr, const uint8_t *alias, uint32_t n, uint32_t u) {
-  uint32_t off = n * (n + 1) / 2;
-  uint32_t j = (uint32_t)(((uint64_t)u * (n + 1)) >> 32);
+  uint32_t off = OR_ALIAS_COLS * n;
+  uint32_t j = u >> 26;
   return u < thr[off + j] ? j : alias[off + j];
 }
 

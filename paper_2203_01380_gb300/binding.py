@@ -81,7 +81,7 @@ class Tuning(ctypes.Structure):
                 ("n", ctypes.c_uint32), ("ms_per_step", ctypes.c_double * 8)]
 
 
-CONTEXT_CANDIDATES = ("vec8", "vec4", "node", "tb2", "tb4")
+CONTEXT_CANDIDATES = ("vec8", "vec4", "node", "tb2", "tb4", "seg8")
 BATCH_CANDIDATES = ("threads256", "threads512", "threads1024")
 
 
@@ -231,7 +231,8 @@ class Lattice:
         return _tuning_dict(t, CONTEXT_CANDIDATES)
 
     def set_step_kernel(self, candidate: int):
-        """ilg_set_step_kernel: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, -1 default."""
+        """ilg_set_step_kernel: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, 5 warp
+        segments of 8-node vectors, -1 default."""
         _check(_lib.ilg_set_step_kernel(self._h, int(candidate)), self._h)
 
     def set_temporal_blocking(self, depth: int):
@@ -515,14 +516,14 @@ def philox(ctr: np.ndarray, seed: int, stream=None) -> np.ndarray:
 
 
 def binomial_table(P: int) -> np.ndarray:
-    out = np.zeros(2080, dtype=np.uint32)
+    out = np.zeros(2016, dtype=np.uint32)
     _check(_lib.ilg_binomial_table(int(P), out))
     return out
 
 
 def alias_table(P: int):
-    thr = np.zeros(2145, dtype=np.uint32)
-    al = np.zeros(2145, dtype=np.uint32)
+    thr = np.zeros(4096, dtype=np.uint32)
+    al = np.zeros(4096, dtype=np.uint32)
     _check(_lib.ilg_alias_table(int(P), thr, al))
     return thr, al
 

@@ -347,43 +347,60 @@ ilg_status ilg_set_temporal_blocking(ilg_ctx* c, uint32_t depth) {
   if (!c) return ILG_E_INVALID;
   if (depth > kMaxTbDepth) return fail(c, ILG_E_INVALID, "temporal blocking depth above 8");
   if (depth >= 2 && c->Q != 5) return fail(c, ILG_E_INVALID, "temporal blocking is for D2Q5 lattices");
-  if (depth >= 2) ILG_CUDA(c, prepare_step_tb_kernel(kTbTile, depth), "cudaFuncSetAttribute");
+  if (depth >= 2) ILG_CUDA(c, prepare_step_tb_kernel(tb_tile(depth), depth), "cudaFuncSetAttribute");
   c->tb_depth = depth >= 2 ? depth : 0;
   return ILG_OK;
 }
 
 namespace {
 
-// Single-step kernels, in the order of the autotuner's candidates.
-enum : int { kKernelVec8 = 0, kKernelVec4 = 1, kKernelNode = 2 };
+// Single-step kernels, numbered as the autotuner's candidates (3 and 4 are the
+// temporal-blocking depths).
+enum : int { kKernelVec8 = 0, kKernelVec4 = 1, kKernelNode = 2, kKernelSeg = 5 };
+
+bool is_single_step(int cand) { return cand <= kKernelNode || cand == kKernelSeg; }
 
 bool kernel_applies(const ilg_ctx* c, const StepArgs& a, int kind) {
   if (kind == kKernelNode) return true;
   if (c->Q == 9 || a.general) return false;  // D2Q9 and the general path run node-parallel
-  return c->p.Lx % (kind == kKernelVec8 ? 8u : 4u) == 0;
+  return c->p.Lx % (kind == kKernelVec4 ? 4u : 8u) == 0;
 }
 
+// resident warps of the row-tiled kernels (3 blocks of 8 warps per SM)
+uint64_t vec_warps(const ilg_ctx* c) { return uint64_t(c->sms) * 3 * 8; }
+
 // the kernel a step runs: the tuned one while it applies to the current state, else
-// the default (8-node vectors where the rows allow, node-parallel otherwise)
+// the default: warp segments where the lattice has at least two segments per
+// resident warp, 8-node row tiles where the rows allow, node-parallel otherwise
 int pick_kernel(const ilg_ctx* c, const StepArgs& a) {
   if (c->kernel_choice >= 0 && kernel_applies(c, a, c->kernel_choice)) return c->kernel_choice;
-  return kernel_applies(c, a, kKernelVec8) ? kKernelVec8 : kKernelNode;
+  if (!kernel_applies(c, a, kKernelVec8)) return kKernelNode;
+  return step_seg_units(c->p.Lx, c->p.Ly) >= 2 * vec_warps(c) ? kKernelSeg : kKernelVec8;
 }
 
 cudaError_t launch_single(const ilg_ctx* c, int kind, const StepArgs& a, const uint16_t* in, uint16_t* out,
                           uint64_t t, unsigned long long* fail_word) {
-  if (c->Q == 9) return launch_step9(a, in, out, uint32_t(t), fail_word, step_grid(c, 3), c->stream);
+  if (c->Q == 9) {
+    const size_t blocks = (c->nodes + step9_threads() - 1) / step9_threads();
+    const size_t cap = size_t(c->sms) * step9_blocks_per_sm();
+    return launch_step9(a, in, out, uint32_t(t), fail_word, int(blocks < cap ? blocks : cap), c->stream);
+  }
   if (kind == kKernelVec8)
     return launch_step_vec(c->Q, a, in, out, uint32_t(t), fail_word, vec_grid(c, step_vec_blocks_per_sm(8)), c->stream,
                            8);
   if (kind == kKernelVec4)
     return launch_step_vec(c->Q, a, in, out, uint32_t(t), fail_word, vec_grid(c, step_vec_blocks_per_sm(4)), c->stream,
                            4);
+  if (kind == kKernelSeg) {
+    const uint64_t blocks = (step_seg_units(c->p.Lx, c->p.Ly) + 7) / 8, cap = vec_warps(c) / 8;
+    return launch_step_seg(c->Q, a, in, out, uint32_t(t), fail_word, int(blocks < cap ? blocks : cap), c->stream);
+  }
   return launch_step(c->Q, a, in, out, uint32_t(t), fail_word, step_grid(c, 3), c->stream);
 }
 
-int tb_grid(const ilg_ctx* c) {
-  const size_t tiles = size_t((c->p.Lx + kTbTile - 1) / kTbTile) * ((c->p.Ly + kTbTile - 1) / kTbTile);
+int tb_grid(const ilg_ctx* c, uint32_t depth) {
+  const uint32_t B = tb_tile(depth);
+  const size_t tiles = size_t((c->p.Lx + B - 1) / B) * ((c->p.Ly + B - 1) / B);
   return int(std::min<size_t>(tiles, size_t(c->sms) * 2));
 }
 
@@ -407,9 +424,9 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   uint64_t t = t0;
   const uint32_t tb = c->tb_depth;
   if (tb >= 2) {
-    const int tgrid = tb_grid(c);
+    const int tgrid = tb_grid(c, tb);
     for (uint32_t k = 0; k + tb <= T; k += tb) {
-      cudaError_t e = launch_step_tb(a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), tb, kTbTile, c->d_fail, tgrid,
+      cudaError_t e = launch_step_tb(a, c->buf[cur], c->buf[cur ^ 1], uint32_t(t), tb, tb_tile(tb), c->d_fail, tgrid,
                                      c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "temporal blocking kernel");
       launch_t.push_back(t);
@@ -447,7 +464,8 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
 
 ilg_status ilg_set_step_kernel(ilg_ctx* c, int32_t candidate) {
   if (!c) return ILG_E_INVALID;
-  if (candidate < -1 || candidate > kKernelNode) return fail(c, ILG_E_INVALID, "candidate must be -1, 0, 1 or 2");
+  if (candidate < -1 || (candidate >= 0 && !is_single_step(candidate)))
+    return fail(c, ILG_E_INVALID, "candidate must be -1, 0, 1, 2 or 5");
   c->kernel_choice = candidate;
   return ILG_OK;
 }
@@ -484,9 +502,9 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
     return cuda_fail(c, e, "autotune scratch");
   }
   // candidates: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, 3 / 4 temporal
-  // blocking of depth 2 / 4 (D2Q5)
+  // blocking of depth 2 / 4 (D2Q5), 5 warp segments of 8-node vectors
   ilg_tuning res{};
-  res.n = 5;
+  res.n = 6;
   for (int k = 0; k < 8; ++k) res.ms_per_step[k] = -1.0;
   auto trial = [&](int cand, double* ms_per_step) -> cudaError_t {
     const uint32_t depth = cand == 3 ? 2u : (cand == 4 ? 4u : 1u);
@@ -494,7 +512,7 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
     uint64_t t = c->t;
     int cur = 0;
     auto one = [&]() -> cudaError_t {
-      cudaError_t r = depth > 1 ? launch_step_tb(a, s[cur], s[cur ^ 1], uint32_t(t), depth, kTbTile, fw, tb_grid(c),
+      cudaError_t r = depth > 1 ? launch_step_tb(a, s[cur], s[cur ^ 1], uint32_t(t), depth, tb_tile(depth), fw, tb_grid(c, depth),
                                                  c->stream)
                                 : launch_single(c, cand, a, s[cur], s[cur ^ 1], t, fw);
       t += depth;
@@ -514,30 +532,32 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
     if (r == cudaSuccess && *c->h_word == ~0ull) *ms_per_step = double(ms) / (double(launches) * depth);
     return r;
   };
-  for (int cand = 0; cand < 5 && e == cudaSuccess; ++cand) {
-    if (cand <= 2 && !kernel_applies(c, a, cand)) continue;
-    if (cand <= 2 && c->Q == 9 && cand != kKernelNode) continue;
-    if (cand >= 3) {
+  for (int cand = 0; cand < 6 && e == cudaSuccess; ++cand) {
+    if (is_single_step(cand) && !kernel_applies(c, a, cand)) continue;
+    if (is_single_step(cand) && c->Q == 9 && cand != kKernelNode) continue;
+    if (!is_single_step(cand)) {
       if (c->Q != 5) continue;
       const uint32_t depth = cand == 3 ? 2u : 4u;
-      if ((e = prepare_step_tb_kernel(kTbTile, depth)) != cudaSuccess) break;
+      if ((e = prepare_step_tb_kernel(tb_tile(depth), depth)) != cudaSuccess) break;
     }
     e = trial(cand, &res.ms_per_step[cand]);
   }
   release();
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune trial");
   int best = -1;
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 6; ++k)
     if (res.ms_per_step[k] >= 0.0 && (best < 0 || res.ms_per_step[k] < res.ms_per_step[best])) best = k;
   if (best < 0) return fail(c, ILG_E_OVERFLOW, "every trial overflowed: no choice made");
-  if (best >= 3) {
+  if (!is_single_step(best)) {
     // temporal blocking; the remaining single steps take the fastest single-step kernel
     int single = -1;
-    for (int k = 0; k < 3; ++k)
-      if (res.ms_per_step[k] >= 0.0 && (single < 0 || res.ms_per_step[k] < res.ms_per_step[single])) single = k;
+    for (int k = 0; k < 6; ++k)
+      if (is_single_step(k) && res.ms_per_step[k] >= 0.0 &&
+          (single < 0 || res.ms_per_step[k] < res.ms_per_step[single]))
+        single = k;
     c->kernel_choice = single;
     c->tb_depth = best == 3 ? 2u : 4u;
-    ILG_CUDA(c, prepare_step_tb_kernel(kTbTile, c->tb_depth), "cudaFuncSetAttribute");
+    ILG_CUDA(c, prepare_step_tb_kernel(tb_tile(c->tb_depth), c->tb_depth), "cudaFuncSetAttribute");
   } else {
     c->kernel_choice = best;
     c->tb_depth = 0;

@@ -149,8 +149,8 @@ __device__ void ring_finalise(const unsigned long long* red, long long* out) {
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(BatchArgs b, StepArgs common) {
   extern __shared__ uint4 smem4[];
-  uint32_t* tables = reinterpret_cast<uint32_t*>(smem4);                     // kDevBlockWords words
-  uint32_t* xbuf = tables + kDevBlockWords;                                   // kBatchExtWords x THREADS
+  uint32_t* tables = reinterpret_cast<uint32_t*>(smem4);                     // kBatchTableWords words
+  uint32_t* xbuf = tables + kBatchTableWords;                                 // kBatchExtWords x THREADS
   uint16_t* ring = reinterpret_cast<uint16_t*>(xbuf + kBatchExtWords * THREADS);  // 2 x 3 x Lmax
   __shared__ uint32_t s_task;
   __shared__ int s_fail;
@@ -180,9 +180,15 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
     a.general = d.general;
     a.particle = d.particle;
 
-    // tables and ring into shared memory
-    const uint4* gt = reinterpret_cast<const uint4*>(b.tables + size_t(r) * kDevBlockWords);
-    for (uint32_t i = tid; i < kDevBlockWords / 4; i += THREADS) smem4[i] = gt[i];
+    // tables (the two alias tables packed one word per column; the particle
+    // sampler's boundaries as they are) and ring into shared memory
+    const uint32_t* gt = b.tables + size_t(r) * kDevBlockWords;
+    if (a.particle) {
+      for (uint32_t i = tid; i < kBatchTableWords / 4; i += THREADS) smem4[i] = reinterpret_cast<const uint4*>(gt)[i];
+    } else {
+      const uint2* g2 = reinterpret_cast<const uint2*>(gt);
+      for (uint32_t i = tid; i < 2 * kDevAliasEntries; i += THREADS) tables[i] = pack_alias4(i, g2[i]);
+    }
     const uint16_t* gs = b.state + d.state_off;
     uint16_t* buf0 = ring;
     uint16_t* buf1 = ring + 3 * b.Lmax;
@@ -216,8 +222,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
         m[0] = n[0];
         m[1] = a.flip ? n[2] : n[1];
         m[2] = a.flip ? n[1] : n[2];
-        if (a.general || !collide_try_fast<3>(a, tables, x, t, m, post)) {
-          collide_general<3, kBatchExtWords, THREADS>(a, tables, x, t, m, post, xbuf + tid);
+        if (a.general || !collide_try_fast<3, Alias4>(a, tables, x, t, m, post)) {
+          collide_general<3, kBatchExtWords, THREADS, Alias4>(a, tables, x, t, m, post, xbuf + tid);
           bad |= post[0] > 65535u || post[1] > 65535u || post[2] > 65535u;
         }
         const uint32_t xp = x + 1 == L ? 0 : x + 1;
@@ -258,18 +264,28 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
 }  // namespace
 
 // Default shape: batches whose rings all have at most kBatchSmallL nodes run on
-// 256-thread blocks, several per SM; others on 1024-thread blocks.  The autotuner
+// 256-thread blocks, several per SM; others on 1024-thread blocks, or 512 where the
+// longest ring does not fit beside 1024 threads' buffers.  The autotuner
 // (ilg_batch_autotune) may pick 256, 512 or 1024 threads instead.
 constexpr int kBatchThreads = 1024;
 constexpr int kBatchSmallThreads = 256;
 constexpr uint32_t kBatchSmallL = 1024;
 
 size_t batch_smem_bytes(uint32_t Lmax, int threads) {
-  return sizeof(uint32_t) * (kDevBlockWords + size_t(kBatchExtWords) * threads) +
+  return sizeof(uint32_t) * (kBatchTableWords + size_t(kBatchExtWords) * threads) +
          sizeof(uint16_t) * 2 * 3 * size_t(Lmax);
 }
 
-uint32_t batch_default_threads(uint32_t Lmax) { return Lmax <= kBatchSmallL ? kBatchSmallThreads : kBatchThreads; }
+// largest dynamic shared memory a shape may ask for (the 227 KB a block may opt into,
+// less room for the kernel's static shared memory)
+constexpr size_t kBatchSmemCap = 223 * 1024;
+
+bool batch_shape_fits(uint32_t Lmax, int threads) { return batch_smem_bytes(Lmax, threads) <= kBatchSmemCap; }
+
+uint32_t batch_default_threads(uint32_t Lmax) {
+  if (Lmax <= kBatchSmallL) return kBatchSmallThreads;
+  return batch_shape_fits(Lmax, kBatchThreads) ? kBatchThreads : kBatchThreads / 2;
+}
 
 template <int THREADS>
 static cudaError_t batch_attr(uint32_t Lmax) {
@@ -278,6 +294,7 @@ static cudaError_t batch_attr(uint32_t Lmax) {
 }
 
 cudaError_t prepare_batch_kernel(uint32_t Lmax, int threads) {
+  if (!batch_shape_fits(Lmax, threads)) return cudaErrorInvalidValue;
   if (threads == 256) return batch_attr<256>(Lmax);
   if (threads == 512) return batch_attr<512>(Lmax);
   if (threads == 1024) return batch_attr<1024>(Lmax);

@@ -12,6 +12,8 @@ namespace ilg {
 
 constexpr uint32_t kBatchMaxL = 10240;  // longest ring (the ring and its copy live in shared memory)
 constexpr int kBatchExtWords = 16;      // extension words per thread in shared memory
+// the ring's alias tables in shared memory, one word per column (Alias4)
+constexpr uint32_t kBatchTableWords = 2 * kDevAliasEntries;
 
 struct ReplicaDesc {
   uint32_t L;           // ring length
@@ -44,6 +46,7 @@ struct BatchArgs {
 };
 
 size_t batch_smem_bytes(uint32_t Lmax, int threads);
+bool batch_shape_fits(uint32_t Lmax, int threads);
 // block shapes: 256, 512 or 1024 threads (ceil(L / threads) nodes per thread and step)
 uint32_t batch_default_threads(uint32_t Lmax);
 cudaError_t prepare_batch_kernel(uint32_t Lmax, int threads);

@@ -16,7 +16,9 @@ namespace ilg {
 
 namespace {
 
-constexpr int kD9Threads = 256;
+// three alias tables (96 KB) per block: two blocks of twelve warps per SM
+constexpr int kD9Threads = 384;
+constexpr int kD9BlocksPerSm = 2;
 
 // velocity order: rest, +x, -x, +y, -y, (+1,+1), (-1,-1), (+1,-1), (-1,+1)
 __device__ __forceinline__ int d9_vx(int i) { return (i == 1 || i == 5 || i == 7) ? 1 : ((i == 2 || i == 6 || i == 8) ? -1 : 0); }
@@ -64,7 +66,7 @@ __device__ __forceinline__ bool collide9_try_fast(const StepArgs& a, const uint3
   uint32_t W[16];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const uint4 w = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | uint32_t(b)), a.rk);
+    const uint4 w = philox_rk(counter(node, t, a.replica, kDevTagStep | uint32_t(b)), a.rk);
     W[4 * b] = w.x;
     W[4 * b + 1] = w.y;
     W[4 * b + 2] = w.z;
@@ -97,7 +99,7 @@ __device__ void collide9_general(const StepArgs& a, const uint32_t* s, uint32_t 
   uint32_t W[16];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const uint4 w = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | uint32_t(b)), a.rk);
+    const uint4 w = philox_rk(counter(node, t, a.replica, kDevTagStep | uint32_t(b)), a.rk);
     W[4 * b] = w.x;
     W[4 * b + 1] = w.y;
     W[4 * b + 2] = w.z;
@@ -137,7 +139,7 @@ __device__ void collide9_general(const StepArgs& a, const uint32_t* s, uint32_t 
   }
 }
 
-__global__ void __launch_bounds__(kD9Threads, 3) step9_kernel(StepArgs a, const uint16_t* __restrict__ in,
+__global__ void __launch_bounds__(kD9Threads, kD9BlocksPerSm) step9_kernel(StepArgs a, const uint16_t* __restrict__ in,
                                                              uint16_t* __restrict__ out, uint32_t t,
                                                              unsigned long long* __restrict__ fail) {
   extern __shared__ uint4 smem4[];
@@ -193,6 +195,9 @@ constexpr size_t kStep9Smem = sizeof(uint32_t) * kDevBlockWords9;
 cudaError_t prepare_step9_kernel() {
   return cudaFuncSetAttribute(step9_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStep9Smem));
 }
+
+uint32_t step9_threads() { return kD9Threads; }
+uint32_t step9_blocks_per_sm() { return kD9BlocksPerSm; }
 
 cudaError_t launch_step9(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t, unsigned long long* fail,
                          int grid, cudaStream_t s) {

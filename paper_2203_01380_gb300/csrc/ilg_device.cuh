@@ -7,19 +7,19 @@
 
 namespace ilg {
 
-constexpr uint32_t kDevNmax = 64;
-constexpr uint32_t kDevAliasEntries = (kDevNmax + 1) * (kDevNmax + 2) / 2;  // rows n = 0..64
+constexpr uint32_t kDevNmax = 63;                                  // trials per alias row
+constexpr uint32_t kDevAliasCols = 64;                             // columns per row: u >> 26
+constexpr uint32_t kDevAliasEntries = (kDevNmax + 1) * kDevAliasCols;  // rows n = 0..63
 // table block: alias table (thinning) | alias table (rest), one uint2 {thr, alias} per column;
 // D2Q9 lattices append the alias table of the axis share
 constexpr uint32_t kDevBlockWords = 2 * kDevAliasEntries * 2;
-// (rounded up to whole 16-byte vectors: the kernels stage the block as uint4)
-constexpr uint32_t kDevBlockWords9 = (3 * kDevAliasEntries * 2 + 3) / 4 * 4;
+constexpr uint32_t kDevBlockWords9 = 3 * kDevAliasEntries * 2;
 static_assert(kDevBlockWords % 4 == 0 && kDevBlockWords9 % 4 == 0, "table blocks are staged as uint4");
 constexpr uint32_t kDevTagStep = 1u << 24;
 constexpr uint32_t kDevTagExt = 2u << 24;
 constexpr uint32_t kDevTagInit = 3u << 24;
 constexpr uint32_t kDevTagParticle = 4u << 24;
-constexpr int kExtWords = 24;        // extension words per thread held in shared memory
+constexpr int kExtWords = 8;         // extension words per thread held in shared memory
 
 // How a probability P/2^32 is drawn: never (P = 0), by table (0 < P < 2^32),
 // always (P = 2^32).
@@ -71,6 +71,14 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t (&rk)[20]) {
   return c;
 }
 
+// Counter of block `tagblock` (purpose tag << 24 | block index) of the random stream
+// of a node at step t.  The step leads and the node follows: the first round then
+// multiplies words that are the same across a launch, and the two step blocks of a
+// node share their second- and third-round multiplies.
+__device__ __forceinline__ uint4 counter(uint32_t node, uint32_t t, uint32_t replica, uint32_t tagblock) {
+  return make_uint4(t, node, replica, tagblock);
+}
+
 __device__ __forceinline__ uint32_t lane_of(const uint4& b, uint32_t i) {
   return i == 0 ? b.x : (i == 1 ? b.y : (i == 2 ? b.z : b.w));
 }
@@ -84,7 +92,7 @@ struct ExtStream {
 __device__ __forceinline__ uint32_t ext_word(const StepArgs& a, ExtStream& e) {
   const uint32_t b = e.next >> 2;
   if (b != e.cached) {
-    e.blk = philox_rk(make_uint4(e.node, e.t, a.replica, kDevTagExt | b), a.rk);
+    e.blk = philox_rk(counter(e.node, e.t, a.replica, kDevTagExt | b), a.rk);
     e.cached = b;
   }
   const uint32_t w = lane_of(e.blk, e.next & 3u);
@@ -100,15 +108,46 @@ __device__ __forceinline__ const uint2* rest_table(const uint32_t* s) {
   return reinterpret_cast<const uint2*>(s) + kDevAliasEntries;
 }
 
-// Binomial(n, P/2^32) for 0 <= n <= 64 with one draw u: column j = floor(u (n+1) / 2^32)
-// of row n (entries n(n+1)/2 ..); j if u is below the column's threshold, else its alias.
+// Binomial(n, P/2^32) for 0 <= n <= 63 with one draw u: column j = u >> 26 of row n
+// (entries 64 n ..), entry 64 n + j = (n << 6) | (u >> 26) in one funnel shift;
+// j if u is below the column's threshold, else its alias.
 __device__ __forceinline__ uint32_t binomial_alias(const uint2* A, uint32_t n, uint32_t u) {
-  const uint32_t j = __umulhi(u, n + 1);
-  const uint2 e = A[((n * (n + 1)) >> 1) + j];
-  return u < e.x ? j : e.y;
+  const uint32_t idx = __funnelshift_l(u, n, 6);
+  const uint2 e = A[idx];
+  return u < e.x ? (idx & (kDevAliasCols - 1)) : e.y;
 }
 
-// Binomial(m, P) for any m: chunks of 64 trials, the first with the slot word,
+// Views of one alias table of the table block, called as draw(n, u).
+// Alias8: the {threshold, alias} pairs as the host builds them (binomial_alias).
+// Alias4: the same table packed into one word per column, for kernels short of
+//   shared memory: (thr - j 2^26) << 6 | alias, or j for a full column.  The draw
+//   compares u's offset within its column, shifted up over six one bits, with the
+//   packed word: below it exactly when the offset is below the column's share
+//   (thr - j 2^26 < 2^26), so the outcome is the same as binomial_alias's.
+struct Alias8 {
+  const uint2* A;
+  __device__ __forceinline__ static Alias8 of(const uint32_t* s, uint32_t which) {
+    return Alias8{reinterpret_cast<const uint2*>(s) + which * kDevAliasEntries};
+  }
+  __device__ __forceinline__ uint32_t operator()(uint32_t n, uint32_t u) const { return binomial_alias(A, n, u); }
+};
+struct Alias4 {
+  const uint32_t* A;
+  __device__ __forceinline__ static Alias4 of(const uint32_t* s, uint32_t which) {
+    return Alias4{s + which * kDevAliasEntries};
+  }
+  __device__ __forceinline__ uint32_t operator()(uint32_t n, uint32_t u) const {
+    const uint32_t e = A[__funnelshift_l(u, n, 6)];
+    return __funnelshift_l(0xFFFFFFFFu, u, 6) < e ? (u >> 26) : (e & (kDevAliasCols - 1));
+  }
+};
+// Alias4 word of entry i (column i mod 64) of a table, from its Alias8 pair.
+__device__ __forceinline__ uint32_t pack_alias4(uint32_t i, uint2 e) {
+  const uint32_t j = i & (kDevAliasCols - 1);
+  return e.y == j ? j : (((e.x - (j << 26)) << 6) | e.y);
+}
+
+// Binomial(m, P) for any m: chunks of 63 trials, the first with the slot word,
 // every further chunk with the next extension word.
 __device__ __forceinline__ uint32_t binomial(uint32_t mode, const uint2* A, uint32_t m, uint32_t slot,
                                              const StepArgs& a, ExtStream& e) {
@@ -132,8 +171,8 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* s, ui
                                         const uint32_t (&m)[Q], uint32_t (&out)[Q]) {
   const uint2* to = thinning_table(s);
   const uint2* tr = rest_table(s);
-  const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
-  const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
+  const uint4 b0 = philox_rk(counter(node, t, a.replica, kDevTagStep | 0u), a.rk);
+  const uint4 b1 = philox_rk(counter(node, t, a.replica, kDevTagStep | 1u), a.rk);
   const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
   ExtStream e{node, t, 0u, 0xFFFFFFFFu, make_uint4(0, 0, 0, 0)};
 
@@ -176,24 +215,24 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* s, ui
 // buffer (word e at xb[e * S]; threads interleaved with stride S, so a warp's
 // accesses hit distinct banks), so a warp runs its blocks together; words beyond K
 // are read lazily.  A probability of 0 or 2^32 draws nothing.
-template <int Q, int K, int S>
+template <int Q, int K, int S, class Tab = Alias8>
 __device__ __forceinline__ void collide_buffered(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
                                                  const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
   static_assert(K % 4 == 0, "whole Philox blocks");
-  const uint2* to = thinning_table(s);
-  const uint2* tr = rest_table(s);
-  auto extra = [](uint32_t mode, uint32_t x) -> uint32_t { return mode == kTable && x > kDevNmax ? (x - 1) >> 6 : 0u; };
+  const Tab to = Tab::of(s, 0);
+  const Tab tr = Tab::of(s, 1);
+  auto extra = [](uint32_t mode, uint32_t x) -> uint32_t { return mode == kTable && x > kDevNmax ? (x - 1) / kDevNmax : 0u; };
   uint32_t need = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) need += extra(a.omega_mode, m[i]);
-  const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
-  const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
+  const uint4 b0 = philox_rk(counter(node, t, a.replica, kDevTagStep | 0u), a.rk);
+  const uint4 b1 = philox_rk(counter(node, t, a.replica, kDevTagStep | 1u), a.rk);
   const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
   uint32_t filled = 0;
   auto gen = [&](uint32_t upto) {
     upto = upto < uint32_t(K) ? upto : uint32_t(K);
     for (; filled < upto; filled += 4) {
-      const uint4 b = philox_rk(make_uint4(node, t, a.replica, kDevTagExt | (filled >> 2)), a.rk);
+      const uint4 b = philox_rk(counter(node, t, a.replica, kDevTagExt | (filled >> 2)), a.rk);
       uint32_t* p = xb + filled * S;
       p[0] = b.x;
       p[S] = b.y;
@@ -208,14 +247,14 @@ __device__ __forceinline__ void collide_buffered(const StepArgs& a, const uint32
     return ext_word(a, lazy);
   };
   uint32_t e = 0;
-  // Binomial(x, P) in chunks of 64 trials: the first with the slot word, the others
+  // Binomial(x, P) in chunks of 63 trials: the first with the slot word, the others
   // with the next extension words
-  auto draw = [&](uint32_t mode, const uint2* A, uint32_t x, uint32_t slot) -> uint32_t {
+  auto draw = [&](uint32_t mode, const Tab& A, uint32_t x, uint32_t slot) -> uint32_t {
     if (mode == kNever) return 0u;
     if (mode == kAlways) return x;
-    uint32_t r = binomial_alias(A, x < kDevNmax ? x : kDevNmax, slot);
+    uint32_t r = A(x < kDevNmax ? x : kDevNmax, slot);
     for (uint32_t left = x > kDevNmax ? x - kDevNmax : 0u; left > 0; left -= (left < kDevNmax ? left : kDevNmax))
-      r += binomial_alias(A, left < kDevNmax ? left : kDevNmax, word(e++));
+      r += A(left < kDevNmax ? left : kDevNmax, word(e++));
     return r;
   };
   gen(need);
@@ -291,7 +330,7 @@ __device__ void collide_particle(const StepArgs& a, const uint32_t* s, uint32_t 
   for (int k = 0; k < Q; ++k) ge[k] = from[k] = 0;
   if (bound(0) < (1ull << 32)) {  // B_0 = 2^32: every particle stays, the words are not needed
     for (uint32_t b = 0; 4 * b < N; ++b) {
-      const uint4 blk = philox_rk(make_uint4(node, t, a.replica, kDevTagParticle | b), a.rk);
+      const uint4 blk = philox_rk(counter(node, t, a.replica, kDevTagParticle | b), a.rk);
 #pragma unroll
       for (uint32_t q = 0; q < 4; ++q) {
         const uint32_t d = 4 * b + q;
@@ -317,11 +356,11 @@ __device__ void collide_particle(const StepArgs& a, const uint32_t* s, uint32_t 
 }
 
 // The general collision in whichever sampler the lattice uses.
-template <int Q, int K, int S>
+template <int Q, int K, int S, class Tab = Alias8>
 __device__ __forceinline__ void collide_general(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
                                                 const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
   if (a.particle) collide_particle<Q>(a, s, node, t, m, out);
-  else collide_buffered<Q, K, S>(a, s, node, t, m, out, xb);
+  else collide_buffered<Q, K, S, Tab>(a, s, node, t, m, out, xb);
 }
 
 // The collision of one node, fast path: every occupation <= 63, at most 63
@@ -330,28 +369,28 @@ __device__ __forceinline__ void collide_general(const StepArgs& a, const uint32_
 // (out undefined) when the node falls outside that domain; the caller then runs
 // collide().  Same result as collide() wherever it returns true.  No result can
 // exceed 65535 here (mass is conserved and at most 5 * 63).
-template <int Q>
+template <int Q, class Tab = Alias8>
 __device__ __forceinline__ bool collide_try_fast(const StepArgs& a, const uint32_t* s, uint32_t node,
                                                  uint32_t t, const uint32_t (&m)[Q], uint32_t (&out)[Q]) {
-  const uint2* to = thinning_table(s);
-  const uint2* tr = rest_table(s);
+  const Tab to = Tab::of(s, 0);
+  const Tab tr = Tab::of(s, 1);
   if (a.omega_mode != kTable || a.rest_mode != kTable) return false;
   uint32_t any = m[0];
 #pragma unroll
   for (int i = 1; i < Q; ++i) any |= m[i];
   if (any >> 6) return false;
-  const uint4 b0 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 0u), a.rk);
-  const uint4 b1 = philox_rk(make_uint4(node, t, a.replica, kDevTagStep | 1u), a.rk);
+  const uint4 b0 = philox_rk(counter(node, t, a.replica, kDevTagStep | 0u), a.rk);
+  const uint4 b1 = philox_rk(counter(node, t, a.replica, kDevTagStep | 1u), a.rk);
   // slot words: thinning 0..Q-1, rest Q, moving Q+1 (and Q+2)
   const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
   uint32_t r[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) r[i] = binomial_alias(to, m[i], W[i]);
+  for (int i = 0; i < Q; ++i) r[i] = to(m[i], W[i]);
   uint32_t removed = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) removed += r[i];
   if (removed >> 6) return false;
-  const uint32_t to_rest = binomial_alias(tr, removed, W[Q]);
+  const uint32_t to_rest = tr(removed, W[Q]);
   const uint32_t moving = removed - to_rest;
   if (moving > 32) return false;
   const uint32_t mask = moving == 32 ? 0xFFFFFFFFu : ((1u << moving) - 1u);

@@ -9,19 +9,23 @@
 
 namespace ilg {
 
-constexpr uint32_t kNmax = 64;                              // trials per binomial table row
-constexpr uint32_t kTableWords = kNmax * (kNmax + 1) / 2;   // 2080 entries
+constexpr uint32_t kNmax = 63;                              // trials per binomial table row
+constexpr uint32_t kTableWords = kNmax * (kNmax + 1) / 2;   // 2016 entries
 constexpr uint32_t kPoissonCap = 4096;                       // entries per Poisson table
 constexpr double kMaxMean = 700.0;                           // largest initial mean
 constexpr uint32_t kMaxTbDepth = 8;                          // temporal blocking: steps per launch
-constexpr uint32_t kTbTile = 48;                             // temporal blocking: tile side
+constexpr uint32_t kTbWindow = 44;                           // temporal blocking: tile + halo per side
+// temporal blocking: output tile side at depth Tb (the window with its halo stays 44
+// nodes wide, so two blocks fit on an SM beside their alias tables)
+constexpr uint32_t tb_tile(uint32_t depth) { return kTbWindow - 2 * depth; }
 
 // Philox purpose tags (top 8 bits of the fourth counter word).
 constexpr uint32_t kTagStep = 1;
 constexpr uint32_t kTagExt = 2;
 constexpr uint32_t kTagInit = 3;
 
-constexpr uint32_t kAliasEntries = (kNmax + 1) * (kNmax + 2) / 2;  // rows n = 0..64
+constexpr uint32_t kAliasCols = 64;                                // columns per alias row
+constexpr uint32_t kAliasEntries = (kNmax + 1) * kAliasCols;       // rows n = 0..63
 struct AliasEntry {
   uint32_t thr;    // draws below the threshold keep the column's own outcome
   uint32_t alias;  // outcome of the other draws of the column
@@ -29,8 +33,7 @@ struct AliasEntry {
 // device table block: alias(thinning) | alias(rest), AliasEntry each
 constexpr uint32_t kBlockWords = 2 * kAliasEntries * 2;
 // D2Q9: alias(thinning) | alias(rest) | alias(axis share)
-// (rounded up to whole 16-byte vectors)
-constexpr uint32_t kBlockWords9 = (3 * kAliasEntries * 2 + 3) / 4 * 4;
+constexpr uint32_t kBlockWords9 = 3 * kAliasEntries * 2;
 
 void build_binomial_table(uint64_t P, uint32_t* T);
 void build_alias_table(uint64_t P, AliasEntry* out);

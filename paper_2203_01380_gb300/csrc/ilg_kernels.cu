@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) init_kernel(InitArgs a, uint16_t* __restr
     uint32_t W[(Q + 3) / 4 * 4];
 #pragma unroll
     for (int b = 0; b < (Q + 3) / 4; ++b) {
-      const uint4 w = philox(make_uint4(node, 0u, a.replica, kDevTagInit | uint32_t(b)), a.key0, a.key1);
+      const uint4 w = philox(counter(node, 0u, a.replica, kDevTagInit | uint32_t(b)), a.key0, a.key1);
       W[4 * b] = w.x;
       W[4 * b + 1] = w.y;
       W[4 * b + 2] = w.z;

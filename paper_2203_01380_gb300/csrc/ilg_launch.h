@@ -31,12 +31,19 @@ uint32_t step_vec_blocks_per_sm(int npt);
 // npt: nodes per thread, 8 (default) or 4 (rows a multiple of npt)
 cudaError_t launch_step_vec(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                             unsigned long long* fail, int grid, cudaStream_t s, int npt = 8);
+// warp-segment form of the 8-node row-tiled step (segments of 8192 nodes of a row,
+// one warp each): step_seg_units = the number of segments of a lattice
+uint64_t step_seg_units(uint32_t Lx, uint32_t Ly);
+cudaError_t launch_step_seg(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
+                            unsigned long long* fail, int grid, cudaStream_t s);
 size_t step_tb_smem_bytes(uint32_t B, uint32_t Tb);
 cudaError_t prepare_step_tb_kernel(uint32_t B, uint32_t Tb);
 cudaError_t launch_step_tb(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t0, uint32_t Tb,
                            uint32_t B, unsigned long long* fail, int grid, cudaStream_t s);
 cudaError_t launch_init(int Q, const InitArgs& a, uint16_t* out, int grid, cudaStream_t s);
 cudaError_t prepare_step9_kernel();  // D2Q9 (ilg_d2q9.cu)
+uint32_t step9_threads();
+uint32_t step9_blocks_per_sm();
 cudaError_t launch_step9(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t, unsigned long long* fail,
                          int grid, cudaStream_t s);
 cudaError_t launch_sums(int Q, const uint16_t* in, uint32_t Lx, uint32_t Ly, unsigned long long* col,

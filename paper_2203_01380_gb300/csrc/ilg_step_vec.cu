@@ -9,7 +9,8 @@
 // (carried), or — at the two ends of a row, where the lattice wraps — from the
 // other end of the same row, so the vectors of the first and last thread are
 // held back until that value exists.  Exchange slots are double-buffered by tile
-// parity, so one barrier per tile suffices.
+// parity, so one barrier per tile suffices.  A second kernel (step_seg_kernel, below)
+// does the same work with warp shuffles and no barrier.
 #include <cuda_runtime.h>
 
 #include "ilg_device.cuh"
@@ -85,41 +86,89 @@ __device__ __forceinline__ void flip(const StepArgs& a, const uint32_t (&n)[Q], 
   }
 }
 
-// the fast-path collision the row-tiled kernel uses
-struct FastCollide {
-  static constexpr uint32_t kSmemWords = kDevBlockWords;  // table block staged in shared memory
-  template <int Q>
-  __device__ __forceinline__ static bool run(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
-                                             const uint32_t (&m)[Q], uint32_t (&post)[Q]) {
-    return collide_try_fast<Q>(a, s, node, t, m, post);
+// Flip and collide the NPT nodes of one vector (x0 .. x0+NPT-1 of the row at
+// rowoff) into the packed post-collision planes P.  The fast path runs for every
+// node; nodes outside its domain (an occupation above 63, more than 63 removed or
+// more than 32 moving) are redone with the general collision, reading their input
+// again, and overwrite their half-words.  bad is set when a result exceeds 65535.
+template <int Q, int NPT>
+__device__ __forceinline__ void collide_vector(const StepArgs& a, const uint32_t* s, const uint16_t* __restrict__ in,
+                                               size_t plane, size_t rowoff, uint32_t x0, uint32_t t,
+                                               Vec<NPT> (&P)[Q], bool& bad) {
+  Vec<NPT> N[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) N[i] = vload<NPT>(in + i * plane + rowoff + x0);
+  if (a.flip) {
+    // the flip F_i(n) = n_{-i} swaps whole opposite planes of the vector
+#pragma unroll
+    for (int j = 0; j < NPT / 2; ++j) {
+      const uint32_t p = N[1].w[j];
+      N[1].w[j] = N[2].w[j];
+      N[2].w[j] = p;
+      if constexpr (Q == 5) {
+        const uint32_t q = N[3].w[j];
+        N[3].w[j] = N[4].w[j];
+        N[4].w[j] = q;
+      }
+    }
   }
-};
-
-// collide one node (occupations m, already flipped) on the fast path (no result
-// there exceeds 65535); returns false when the node needs the general collision
-// (post is then undefined: the general pass overwrites the node's half-words)
-template <int Q, class Coll>
-__device__ __forceinline__ bool node_update(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
-                                            const uint32_t (&m)[Q], uint32_t (&post)[Q]) {
-  return Coll::template run<Q>(a, s, node, t, m, post);
+  uint32_t slow = 0;  // nodes that need the general collision
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    uint32_t n[Q], post[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) n[i] = half(N[i].w, k);
+    if (!collide_try_fast<Q>(a, s, uint32_t(rowoff) + x0 + k, t, n, post)) slow |= 1u << k;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (k & 1) P[i].w[k >> 1] = __byte_perm(P[i].w[k >> 1], post[i], 0x5410);
+      else P[i].w[k >> 1] = post[i];
+    }
+  }
+  while (slow) {
+    const int k = __ffs(slow) - 1;
+    slow &= slow - 1;
+    const size_t at = rowoff + x0 + k;
+    uint32_t n[Q], m[Q], post[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) n[i] = in[i * plane + at];
+    flip<Q>(a, n, m);
+    collide<Q>(a, s, uint32_t(at), t, m, post);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      bad |= post[i] > 65535u;
+      const uint32_t v = post[i] & 0xFFFFu;
+#pragma unroll
+      for (int kk = 0; kk < NPT; ++kk)
+        if (kk == k) {
+          const uint32_t sh = 16 * (kk & 1);
+          P[i].w[kk >> 1] = (P[i].w[kk >> 1] & ~(0xFFFFu << sh)) | (v << sh);
+        }
+    }
+  }
 }
 
-template <int Q, int NPT, bool UNROLL, int MINB, class Coll = FastCollide, int THREADS = kVecThreads>
-__global__ void __launch_bounds__(THREADS, MINB)
+// stage the table block, read the overflow word; false when an earlier launch of the
+// same call overflowed (this one then does nothing)
+__device__ __forceinline__ bool vec_prologue(const StepArgs& a, uint4* smem4, const unsigned long long* fail) {
+  __shared__ int skip;
+  if (threadIdx.x == 0) skip = (*reinterpret_cast<const volatile unsigned long long*>(fail) != ~0ull);
+  const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
+  for (uint32_t i = threadIdx.x; i < kDevBlockWords / 4; i += blockDim.x) smem4[i] = g4[i];
+  __syncthreads();
+  return !skip;
+}
+
+template <int Q, int NPT, int MINB>
+__global__ void __launch_bounds__(kVecThreads, MINB)
     step_vec_kernel(StepArgs a, const uint16_t* __restrict__ in, uint16_t* __restrict__ out, uint32_t t,
                     unsigned long long* __restrict__ fail) {
-  constexpr int kVecThreads = THREADS;
   extern __shared__ uint4 smem4[];
   __shared__ uint32_t xs1[2][kVecThreads];  // +x value of each thread's last node
   __shared__ uint32_t xs2[2][kVecThreads];  // -x value of each thread's first node
-  __shared__ int skip;
-  uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
+  if (!vec_prologue(a, smem4, fail)) return;
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(smem4);
   const int tid = threadIdx.x;
-  if (tid == 0) skip = (*reinterpret_cast<volatile unsigned long long*>(fail) != ~0ull);
-  const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
-  for (uint32_t i = tid; i < Coll::kSmemWords / 4; i += blockDim.x) smem4[i] = g4[i];
-  __syncthreads();
-  if (skip) return;
 
   const uint32_t Lx = a.Lx, Ly = a.Ly;
   const size_t plane = size_t(Lx) * Ly;
@@ -142,87 +191,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
       const uint32_t x0 = v * NPT;
       Vec<NPT> P[Q];
       if (active) {
-        Vec<NPT> N[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) N[i] = vload<NPT>(in + i * plane + rowoff + x0);
-        if (a.flip) {
-          // the flip F_i(n) = n_{-i} swaps whole opposite planes of the vector
-#pragma unroll
-          for (int j = 0; j < NPT / 2; ++j) {
-            const uint32_t p = N[1].w[j];
-            N[1].w[j] = N[2].w[j];
-            N[2].w[j] = p;
-            if constexpr (Q == 5) {
-              const uint32_t q = N[3].w[j];
-              N[3].w[j] = N[4].w[j];
-              N[4].w[j] = q;
-            }
-          }
-        }
-        uint32_t slow = 0;  // nodes that need the general collision
-        if constexpr (UNROLL) {
-#pragma unroll
-          for (int k = 0; k < NPT; ++k) {
-            uint32_t n[Q], post[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) n[i] = half(N[i].w, k);
-            if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + k, t, n, post)) slow |= 1u << k;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-              if (k & 1) P[i].w[k >> 1] = __byte_perm(P[i].w[k >> 1], post[i], 0x5410);
-              else P[i].w[k >> 1] = post[i];
-            }
-          }
-        } else {
-          // rolled over the words: the word in use is always w[0]; inputs move down
-          // one word per pass, finished output words enter at the top
-#pragma unroll 1
-          for (int j = 0; j < NPT / 2; ++j) {
-            uint32_t acc[Q];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              uint32_t n[Q], post[Q];
-#pragma unroll
-              for (int i = 0; i < Q; ++i) n[i] = h ? (N[i].w[0] >> 16) : (N[i].w[0] & 0xFFFFu);
-              if (!node_update<Q, Coll>(a, s, uint32_t(rowoff) + x0 + 2 * j + h, t, n, post))
-                slow |= 1u << (2 * j + h);
-#pragma unroll
-              for (int i = 0; i < Q; ++i) acc[i] = h ? __byte_perm(acc[i], post[i], 0x5410) : post[i];
-            }
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-#pragma unroll
-              for (int q = 0; q < NPT / 2 - 1; ++q) {
-                N[i].w[q] = N[i].w[q + 1];
-                P[i].w[q] = P[i].w[q + 1];
-              }
-              P[i].w[NPT / 2 - 1] = acc[i];
-            }
-          }
-        }
-        // rare: nodes with an occupation above 64, more than 64 removed or more than
-        // 32 moving particles take the general collision (extension words)
-        while (slow) {
-          const int k = __ffs(slow) - 1;
-          slow &= slow - 1;
-          const size_t at = rowoff + x0 + k;
-          uint32_t n[Q], m[Q], post[Q];
-#pragma unroll
-          for (int i = 0; i < Q; ++i) n[i] = in[i * plane + at];
-          flip<Q>(a, n, m);
-          collide<Q>(a, s, uint32_t(at), t, m, post);
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            bad |= post[i] > 65535u;
-            const uint32_t v = post[i] & 0xFFFFu;
-#pragma unroll
-            for (int kk = 0; kk < NPT; ++kk)
-              if (kk == k) {
-                const uint32_t sh = 16 * (kk & 1);
-                P[i].w[kk >> 1] = (P[i].w[kk >> 1] & ~(0xFFFFu << sh)) | (v << sh);
-              }
-          }
-        }
+        collide_vector<Q, NPT>(a, s, in, plane, rowoff, x0, t, P, bad);
         vstore<NPT>(out + rowoff + x0, P[0]);
         if constexpr (Q == 5) {
           vstore<NPT>(out + 3 * plane + size_t(yp) * Lx + x0, P[3]);
@@ -267,19 +236,115 @@ __global__ void __launch_bounds__(THREADS, MINB)
   if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
 }
 
+// Warp-segment form of the same step: no block-wide exchange.  Each warp takes
+// segments of one row in turn (kSegTiles x 32 vectors each, grid-stride over all
+// segments of the lattice) and walks its segment left to right, 32 vectors at a
+// time.  Neighbouring vectors of a warp tile trade their edge values by shuffles;
+// lane 0's left value is carried from the previous tile's lane 31, lane 31's -x
+// vector waits in registers for the next tile's first node.  The two values from
+// outside the segment (the +x result of the node left of it, the -x result of the
+// node right of it, periodic in x) are recomputed by lanes 0 and 1 before the walk:
+// every random number is keyed by node and step, so the recomputed node gives the
+// same bits as where it is owned.
+constexpr uint32_t kSegTiles = 32;  // warp tiles per segment: 1024 vectors
+
+template <int Q, int NPT, int MINB>
+__global__ void __launch_bounds__(kVecThreads, MINB)
+    step_seg_kernel(StepArgs a, const uint16_t* __restrict__ in, uint16_t* __restrict__ out, uint32_t t,
+                    unsigned long long* __restrict__ fail) {
+  extern __shared__ uint4 smem4[];
+  if (!vec_prologue(a, smem4, fail)) return;
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(smem4);
+  constexpr unsigned kFull = 0xFFFFFFFFu;
+  const uint32_t Lx = a.Lx, Ly = a.Ly;
+  const size_t plane = size_t(Lx) * Ly;
+  const uint32_t vpr = Lx / NPT;
+  constexpr uint32_t seg_v = 32u * kSegTiles;             // vectors per segment
+  const uint32_t segs = (vpr + seg_v - 1) / seg_v;        // segments per row
+  const uint32_t units = Ly * segs;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  bool bad = false;
+
+  for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nwarps) {
+    const uint32_t y = u / segs, g = u - y * segs;
+    const uint32_t v0 = g * seg_v;
+    const uint32_t v1 = v0 + seg_v < vpr ? v0 + seg_v : vpr;
+    const size_t rowoff = size_t(y) * Lx;
+    const uint32_t yp = (Q == 5) ? (y + 1 == Ly ? 0 : y + 1) : 0;
+    const uint32_t ym = (Q == 5) ? (y == 0 ? Ly - 1 : y - 1) : 0;
+    uint32_t edge = 0;
+    if (lane < 2) {
+      const uint32_t xe = lane == 0 ? (v0 == 0 ? Lx - 1 : v0 * NPT - 1) : (v1 == vpr ? 0 : v1 * NPT);
+      const size_t at = rowoff + xe;
+      uint32_t n[Q], m[Q], post[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) n[i] = in[i * plane + at];
+      flip<Q>(a, n, m);
+      if (!collide_try_fast<Q>(a, s, uint32_t(at), t, m, post)) collide<Q>(a, s, uint32_t(at), t, m, post);
+      edge = lane == 0 ? post[1] : post[2];
+    }
+    uint32_t carry = __shfl_sync(kFull, edge, 0);           // left value of the tile's lane 0
+    const uint32_t seg_right = __shfl_sync(kFull, edge, 1);  // right value of the segment's last vector
+    Vec<NPT> held_mx;                                       // lane 31: -x vector waiting for the next tile
+    for (uint32_t vb = v0; vb < v1; vb += 32) {
+      const uint32_t v = vb + lane;
+      const bool active = v < v1;
+      const uint32_t x0 = v * NPT;
+      Vec<NPT> P[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < NPT / 2; ++j) P[i].w[j] = 0;
+      if (active) {
+        collide_vector<Q, NPT>(a, s, in, plane, rowoff, x0, t, P, bad);
+        vstore<NPT>(out + rowoff + x0, P[0]);
+        if constexpr (Q == 5) {
+          vstore<NPT>(out + 3 * plane + size_t(yp) * Lx + x0, P[3]);
+          vstore<NPT>(out + 4 * plane + size_t(ym) * Lx + x0, P[4]);
+        }
+      }
+      // +x: the left neighbour's last node
+      const uint32_t last_px = half(P[1].w, NPT - 1);
+      uint32_t left = __shfl_up_sync(kFull, last_px, 1);
+      if (lane == 0) left = carry;
+      carry = __shfl_sync(kFull, last_px, 31);
+      // -x: the right neighbour's first node
+      const uint32_t first_mx = half(P[2].w, 0);
+      const uint32_t right = __shfl_down_sync(kFull, first_mx, 1);
+      const uint32_t tile_first = __shfl_sync(kFull, first_mx, 0);
+      if (lane == 31 && vb > v0)
+        vstore<NPT>(out + 2 * plane + rowoff + size_t(vb - 1) * NPT, shift_down<NPT>(held_mx, tile_first));
+      if (active) {
+        vstore<NPT>(out + plane + rowoff + x0, shift_up<NPT>(P[1], left));
+        if (v + 1 == v1) vstore<NPT>(out + 2 * plane + rowoff + x0, shift_down<NPT>(P[2], seg_right));
+        else if (lane < 31) vstore<NPT>(out + 2 * plane + rowoff + x0, shift_down<NPT>(P[2], right));
+        else held_mx = P[2];
+      }
+    }
+  }
+  if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
+}
+
 constexpr size_t kVecSmem = sizeof(uint32_t) * kDevBlockWords;
 constexpr int kNPT = 8;
-constexpr bool kUnroll = true;
 constexpr int kMinBlocks = 3;
 
-// second shape for the autotuner: 4 nodes per thread, 4 blocks per SM
+// second shape for the autotuner: 4 nodes per thread (as many blocks per SM as the
+// tables in shared memory allow: 3)
 constexpr int kNPT4 = 4;
-constexpr int kMinBlocks4 = 4;
+constexpr int kMinBlocks4 = 3;
 
 template <int Q, int NPT, int MINB>
 static cudaError_t vec_attr() {
-  return cudaFuncSetAttribute(step_vec_kernel<Q, NPT, kUnroll, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(kVecSmem));
+  cudaError_t e = cudaFuncSetAttribute(step_vec_kernel<Q, NPT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(kVecSmem));
+  if constexpr (NPT == kNPT) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(step_seg_kernel<Q, NPT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(kVecSmem));
+  }
+  return e;
 }
 
 cudaError_t prepare_step_vec_kernels() {
@@ -296,12 +361,24 @@ uint32_t step_vec_blocks_per_sm(int npt) { return npt == kNPT4 ? kMinBlocks4 : k
 cudaError_t launch_step_vec(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                             unsigned long long* fail, int grid, cudaStream_t s, int npt) {
   if (npt == kNPT4) {
-    if (Q == 3) step_vec_kernel<3, kNPT4, kUnroll, kMinBlocks4><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
-    else step_vec_kernel<5, kNPT4, kUnroll, kMinBlocks4><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+    if (Q == 3) step_vec_kernel<3, kNPT4, kMinBlocks4><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+    else step_vec_kernel<5, kNPT4, kMinBlocks4><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
   } else {
-    if (Q == 3) step_vec_kernel<3, kNPT, kUnroll, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
-    else step_vec_kernel<5, kNPT, kUnroll, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+    if (Q == 3) step_vec_kernel<3, kNPT, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+    else step_vec_kernel<5, kNPT, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
   }
+  return cudaGetLastError();
+}
+
+uint64_t step_seg_units(uint32_t Lx, uint32_t Ly) {
+  const uint32_t vpr = Lx / kNPT, seg_v = 32 * kSegTiles;
+  return uint64_t(Ly) * ((vpr + seg_v - 1) / seg_v);
+}
+
+cudaError_t launch_step_seg(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
+                            unsigned long long* fail, int grid, cudaStream_t s) {
+  if (Q == 3) step_seg_kernel<3, kNPT, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
+  else step_seg_kernel<5, kNPT, kMinBlocks><<<grid, kVecThreads, kVecSmem, s>>>(a, in, out, t, fail);
   return cudaGetLastError();
 }
 

@@ -41,17 +41,19 @@ void build_binomial_table(uint64_t P, uint32_t* T) {
 }
 
 // Alias tables (Walker; Vose's construction carried out in integers) realising
-// the integer pmf of each CDF row exactly.  Row n (0..kNmax) has n+1 columns at
-// entry offset n(n+1)/2; column j owns the draws u with floor(u (n+1) / 2^32) = j,
-// i.e. [ceil(j 2^32/(n+1)), ceil((j+1) 2^32/(n+1))).  The draw yields j when u is
-// below the column's threshold, its alias otherwise.
+// the integer pmf of each CDF row exactly.  Row n (0..kNmax) has kAliasCols = 64
+// columns at entry offset 64 n; column j owns the 2^26 draws u with u >> 26 = j.
+// Outcomes n+1..63 have weight zero, so their columns go wholly to an alias.  The
+// draw yields j when u is below the column's threshold, its alias otherwise.
 void build_alias_table(uint64_t P, AliasEntry* out) {
+  constexpr uint64_t kColumn = uint64_t(1) << 26;  // draws per column
   std::vector<uint32_t> cdf(kTableWords);
   build_binomial_table(P, cdf.data());
-  std::vector<uint64_t> weight(kNmax + 1), start(kNmax + 2);
+  std::vector<uint64_t> weight(kAliasCols);
   std::vector<uint32_t> under, over;
   for (uint32_t n = 0; n <= kNmax; ++n) {
-    AliasEntry* row = out + n * (n + 1) / 2;
+    AliasEntry* row = out + n * kAliasCols;
+    std::fill(weight.begin(), weight.end(), 0);
     uint64_t below = 0;
     for (uint32_t k = 0; k < n; ++k) {
       const uint64_t c = cdf[n * (n - 1) / 2 + k];
@@ -59,28 +61,24 @@ void build_alias_table(uint64_t P, AliasEntry* out) {
       below = c;
     }
     weight[n] = (uint64_t(1) << 32) - below;
-    for (uint32_t j = 0; j <= n + 1; ++j) start[j] = ((uint64_t(j) << 32) + n) / (n + 1);
     under.clear();
     over.clear();
-    for (uint32_t j = 0; j <= n; ++j) {
+    for (uint32_t j = 0; j < kAliasCols; ++j) {
       row[j].thr = 0;
       row[j].alias = j;
-      const uint64_t size = start[j + 1] - start[j];
-      if (weight[j] < size) under.push_back(j);
-      else if (weight[j] > size) over.push_back(j);
+      if (weight[j] < kColumn) under.push_back(j);
+      else if (weight[j] > kColumn) over.push_back(j);
     }
     while (!under.empty() && !over.empty()) {
       const uint32_t l = under.back();
       under.pop_back();
       const uint32_t g = over.back();
       over.pop_back();
-      const uint64_t lsize = start[l + 1] - start[l];
-      row[l].thr = uint32_t(start[l] + weight[l]);
+      row[l].thr = uint32_t(uint64_t(l) * kColumn + weight[l]);
       row[l].alias = g;
-      weight[g] -= lsize - weight[l];
-      const uint64_t gsize = start[g + 1] - start[g];
-      if (weight[g] < gsize) under.push_back(g);
-      else if (weight[g] > gsize) over.push_back(g);
+      weight[g] -= kColumn - weight[l];
+      if (weight[g] < kColumn) under.push_back(g);
+      else if (weight[g] > kColumn) over.push_back(g);
     }
   }
 }

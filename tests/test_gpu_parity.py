@@ -329,6 +329,20 @@ def test_set_state_high_mass_takes_general_path(B):
     assert t == 16 and np.array_equal(got, O.Lattice(**cfg).run(s_hi, 11, 5))
 
 
+@pytest.mark.parametrize("lattice,Lx,Ly,omega", [(1, 128, 1, 1.0), (2, 64, 24, 1.5), (2, 37, 29, 0.7),
+                                                 (3, 24, 20, 1.0), (3, 19, 13, 1.6)])
+def test_chunk_boundary_occupations(B, lattice, Lx, Ly, omega):
+    """Occupations on both sides of the alias rows' limit (63 trials per draw) and of
+    the 32-particle direction groups: the fast path's edges, one and two extension
+    chunks, and their mix within a row and a vector."""
+    Q = {1: 3, 2: 5, 3: 9}[lattice]
+    edges = np.array([0, 1, 31, 32, 33, 62, 63, 64, 65, 125, 126, 127, 128, 189, 190], dtype=np.uint16)
+    s0 = np.random.default_rng(lattice * 7 + Lx).choice(edges, size=(Q, Ly, Lx)).astype(np.uint16)
+    cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, n0=10.0, omega_eff=omega, seed=12, replica=3)
+    got = gpu_run(B, cfg, 3, state=s0, t0=5)
+    assert np.array_equal(got, O.Lattice(**cfg).run(s0, 5, 3))
+
+
 # ---------------------------------------------------------------- particle sampler
 PARTICLE_CASES = [
     # lattice, Lx, Ly, omega_eff, mean, hot

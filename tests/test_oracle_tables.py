@@ -46,7 +46,7 @@ def test_binomial_table_extremes():
         assert T.min() >= 0 and T.max() <= 0xFFFFFFFF
     # p = 1/2 is dyadic: every entry is exact
     T = O.binomial_table(1 << 31)
-    for n in (1, 2, 5, 31, 64):
+    for n in (1, 2, 5, 31, 63):
         row = T[n * (n - 1) // 2: n * (n - 1) // 2 + n]
         ref = exact_binomial_cdf_scaled(n, 1 << 31)
         assert [int(v) for v in row] == ref
@@ -89,13 +89,13 @@ def test_poisson_table_exact(lam):
 
 def alias_induced_weights(thr, al, n):
     """Exact number of 32-bit draws u that the alias row n maps to each outcome:
-    column j = floor(u (n+1) / 2^32) covers [a_j, a_{j+1}), a_j = ceil(j 2^32 / (n+1));
-    u < thr[j] gives j, else alias[j]."""
-    off = n * (n + 1) // 2
-    cnt = [0] * (n + 1)
-    for j in range(n + 1):
-        a0 = -((-(j << 32)) // (n + 1))
-        a1 = -((-((j + 1) << 32)) // (n + 1))
+    column j = u >> 26 (64 columns) covers [j 2^26, (j+1) 2^26); u < thr[j] gives j,
+    else alias[j].  Outcomes above n must get no draw."""
+    cols = O.ALIAS_COLS
+    off = n * cols
+    cnt = [0] * cols
+    for j in range(cols):
+        a0, a1 = j << 26, (j + 1) << 26
         t = int(thr[off + j])
         alias = int(al[off + j])
         if alias == j:
@@ -104,7 +104,8 @@ def alias_induced_weights(thr, al, n):
             assert a0 <= t <= a1
             cnt[j] += t - a0
             cnt[alias] += a1 - t
-    return cnt
+    assert all(c == 0 for c in cnt[n + 1:]), (n, cnt[n + 1:])
+    return cnt[:n + 1]
 
 
 @pytest.mark.parametrize("p", [1e-9, 0.2, 1.0 / 3.0, 0.5, 0.9, 0.999])
