@@ -182,13 +182,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
 
     // tables (the two alias tables packed one word per column; the particle
     // sampler's boundaries as they are) and ring into shared memory
-    const uint32_t* gt = b.tables + size_t(r) * kDevBlockWords;
-    if (a.particle) {
-      for (uint32_t i = tid; i < kBatchTableWords / 4; i += THREADS) smem4[i] = reinterpret_cast<const uint4*>(gt)[i];
-    } else {
-      const uint2* g2 = reinterpret_cast<const uint2*>(gt);
-      for (uint32_t i = tid; i < 2 * kDevAliasEntries; i += THREADS) tables[i] = pack_alias4(i, g2[i]);
-    }
+    stage_tables4(b.tables + size_t(r) * kDevBlockWords, tables, a.particle != 0);
     const uint16_t* gs = b.state + d.state_off;
     uint16_t* buf0 = ring;
     uint16_t* buf1 = ring + 3 * b.Lmax;

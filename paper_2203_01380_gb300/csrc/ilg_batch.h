@@ -13,7 +13,7 @@ namespace ilg {
 constexpr uint32_t kBatchMaxL = 10240;  // longest ring (the ring and its copy live in shared memory)
 constexpr int kBatchExtWords = 16;      // extension words per thread in shared memory
 // the ring's alias tables in shared memory, one word per column (Alias4)
-constexpr uint32_t kBatchTableWords = 2 * kDevAliasEntries;
+constexpr uint32_t kBatchTableWords = kDevTableWords4;
 
 struct ReplicaDesc {
   uint32_t L;           // ring length

@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kD9Threads, kD9BlocksPerSm) step9_kernel(StepA
   uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
   if (threadIdx.x == 0) skip = (*reinterpret_cast<volatile unsigned long long*>(fail) != ~0ull);
   const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
+#pragma unroll 8
   for (uint32_t i = threadIdx.x; i < kDevBlockWords9 / 4; i += blockDim.x) smem4[i] = g4[i];
   __syncthreads();
   if (skip) return;

@@ -10,16 +10,21 @@ namespace ilg {
 constexpr uint32_t kDevNmax = 63;                                  // trials per alias row
 constexpr uint32_t kDevAliasCols = 64;                             // columns per row: u >> 26
 constexpr uint32_t kDevAliasEntries = (kDevNmax + 1) * kDevAliasCols;  // rows n = 0..63
-// table block: alias table (thinning) | alias table (rest), one uint2 {thr, alias} per column;
-// D2Q9 lattices append the alias table of the axis share
-constexpr uint32_t kDevBlockWords = 2 * kDevAliasEntries * 2;
+// table block: alias table (thinning) | alias table (rest), one uint2 {thr, alias} per
+// column (kDevStagedWords words, what most kernels stage), then for D1Q3 / D2Q5 the
+// same two tables packed one word per column (Alias4, kDevTableWords4 words);
+// D2Q9 lattices have the alias table of the axis share as a third and no packed form
+constexpr uint32_t kDevStagedWords = 2 * kDevAliasEntries * 2;
+constexpr uint32_t kDevTableWords4 = 2 * kDevAliasEntries;
+constexpr uint32_t kDevBlockWords = kDevStagedWords + kDevTableWords4;
 constexpr uint32_t kDevBlockWords9 = 3 * kDevAliasEntries * 2;
-static_assert(kDevBlockWords % 4 == 0 && kDevBlockWords9 % 4 == 0, "table blocks are staged as uint4");
+static_assert(kDevStagedWords % 4 == 0 && kDevBlockWords % 4 == 0 && kDevBlockWords9 % 4 == 0,
+              "table blocks are staged as uint4");
 constexpr uint32_t kDevTagStep = 1u << 24;
 constexpr uint32_t kDevTagExt = 2u << 24;
 constexpr uint32_t kDevTagInit = 3u << 24;
 constexpr uint32_t kDevTagParticle = 4u << 24;
-constexpr int kExtWords = 8;         // extension words per thread held in shared memory
+constexpr int kExtWords = 24;        // extension words per thread held in shared memory
 
 // How a probability P/2^32 is drawn: never (P = 0), by table (0 < P < 2^32),
 // always (P = 2^32).
@@ -141,10 +146,15 @@ struct Alias4 {
     return __funnelshift_l(0xFFFFFFFFu, u, 6) < e ? (u >> 26) : (e & (kDevAliasCols - 1));
   }
 };
-// Alias4 word of entry i (column i mod 64) of a table, from its Alias8 pair.
-__device__ __forceinline__ uint32_t pack_alias4(uint32_t i, uint2 e) {
-  const uint32_t j = i & (kDevAliasCols - 1);
-  return e.y == j ? j : (((e.x - (j << 26)) << 6) | e.y);
+
+// Stage a D1Q3 / D2Q5 lattice's table block (global memory) into shared memory as
+// kDevTableWords4 words: its packed alias tables, or, for the particle sampler, the
+// block's first words (they hold the boundaries B_0..B_Q).  The caller synchronises
+// the block afterwards.
+__device__ __forceinline__ void stage_tables4(const uint32_t* __restrict__ g, uint32_t* s, bool particle) {
+  const uint4* g4 = reinterpret_cast<const uint4*>(particle ? g : g + kDevStagedWords);
+#pragma unroll 8
+  for (uint32_t i = threadIdx.x; i < kDevTableWords4 / 4; i += blockDim.x) reinterpret_cast<uint4*>(s)[i] = g4[i];
 }
 
 // Binomial(m, P) for any m: chunks of 63 trials, the first with the slot word,

@@ -30,8 +30,10 @@ struct AliasEntry {
   uint32_t thr;    // draws below the threshold keep the column's own outcome
   uint32_t alias;  // outcome of the other draws of the column
 };
-// device table block: alias(thinning) | alias(rest), AliasEntry each
-constexpr uint32_t kBlockWords = 2 * kAliasEntries * 2;
+// device table block: alias(thinning) | alias(rest), AliasEntry each, then the same
+// two tables packed one word per entry (D1Q3, D2Q5)
+constexpr uint32_t kPackedOffset = 2 * kAliasEntries * 2;
+constexpr uint32_t kBlockWords = kPackedOffset + 2 * kAliasEntries;
 // D2Q9: alias(thinning) | alias(rest) | alias(axis share)
 constexpr uint32_t kBlockWords9 = 3 * kAliasEntries * 2;
 

@@ -24,10 +24,9 @@ __global__ void __launch_bounds__(kStepThreads, 3) step_kernel(StepArgs a, const
   extern __shared__ uint4 smem4[];
   __shared__ int skip;
   uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
-  uint32_t* xb = s + kDevBlockWords + threadIdx.x;  // this thread's extension words
+  uint32_t* xb = s + kDevTableWords4 + threadIdx.x;  // this thread's extension words
   if (threadIdx.x == 0) skip = (*reinterpret_cast<volatile unsigned long long*>(fail) != ~0ull);
-  const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
-  for (uint32_t i = threadIdx.x; i < kDevBlockWords / 4; i += blockDim.x) smem4[i] = g4[i];
+  stage_tables4(a.tables, s, a.particle != 0);  // packed: room for the extension words
   __syncthreads();
   if (skip) return;
 
@@ -52,8 +51,8 @@ __global__ void __launch_bounds__(kStepThreads, 3) step_kernel(StepArgs a, const
       m[3] = a.flip ? n[4] : n[3];
       m[4] = a.flip ? n[3] : n[4];
     }
-    if (a.general || !collide_try_fast<Q>(a, s, node, t, m, post)) {
-      collide_general<Q, kExtWords, kStepThreads>(a, s, node, t, m, post, xb);
+    if (a.general || !collide_try_fast<Q, Alias4>(a, s, node, t, m, post)) {
+      collide_general<Q, kExtWords, kStepThreads, Alias4>(a, s, node, t, m, post, xb);
 #pragma unroll
       for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
     }
@@ -73,7 +72,7 @@ __global__ void __launch_bounds__(kStepThreads, 3) step_kernel(StepArgs a, const
   if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
 }
 
-constexpr size_t kStepSmem = sizeof(uint32_t) * (kDevBlockWords + kExtWords * kStepThreads);
+constexpr size_t kStepSmem = sizeof(uint32_t) * (kDevTableWords4 + kExtWords * kStepThreads);
 
 cudaError_t prepare_step_kernels() {
   cudaError_t e = cudaFuncSetAttribute(step_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStepSmem));

@@ -38,8 +38,8 @@ __device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s,
       m[3] = a.flip ? n[4] : n[3];
       m[4] = a.flip ? n[3] : n[4];
     }
-    if (a.general || !collide_try_fast<Q>(a, s, uint32_t(at), t, m, post)) {
-      collide_general<Q, kExtWords, kMultiThreads>(a, s, uint32_t(at), t, m, post, xb);
+    if (a.general || !collide_try_fast<Q, Alias4>(a, s, uint32_t(at), t, m, post)) {
+      collide_general<Q, kExtWords, kMultiThreads, Alias4>(a, s, uint32_t(at), t, m, post, xb);
 #pragma unroll
       for (int k = 0; k < Q; ++k) bad |= post[k] > 65535u;
     }
@@ -79,8 +79,7 @@ __global__ void __launch_bounds__(kMultiThreads, kMultiBlocksPerSm) multi_step_k
     const WorkItem w = ma.items[item];
     const LatDesc d = ma.lat[w.lattice];
     if (int(w.lattice) != loaded) {
-      const uint4* g4 = reinterpret_cast<const uint4*>(d.tables);
-      for (uint32_t i = threadIdx.x; i < kDevBlockWords / 4; i += blockDim.x) smem4[i] = g4[i];
+      stage_tables4(d.tables, s, d.particle != 0);  // packed: room for the extension words
       loaded = int(w.lattice);
     }
     __syncthreads();
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(kMultiThreads, kMultiBlocksPerSm) multi_step_k
     const uint16_t* in = odd ? d.buf1 : d.buf0;
     uint16_t* out = odd ? d.buf0 : d.buf1;
     bool bad = false;
-    step_nodes<Q>(a, s, in, out, w.node0, w.node1, t, bad, s + kDevBlockWords + threadIdx.x);
+    step_nodes<Q>(a, s, in, out, w.node0, w.node1, t, bad, s + kDevTableWords4 + threadIdx.x);
     if (bad) atomicMin(ma.fail + w.lattice, sub);
     __syncthreads();  // the tables and s_item stay in use until every thread is done
   }
@@ -106,7 +105,7 @@ __global__ void __launch_bounds__(kMultiThreads, kMultiBlocksPerSm) multi_step_k
 
 }  // namespace
 
-size_t multi_smem_bytes() { return sizeof(uint32_t) * (kDevBlockWords + kExtWords * kMultiThreads); }
+size_t multi_smem_bytes() { return sizeof(uint32_t) * (kDevTableWords4 + kExtWords * kMultiThreads); }
 
 cudaError_t prepare_multi_kernel() {
   return cudaFuncSetAttribute(multi_step_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kTbThreads, 2) step_tb_kernel(StepArgs a, cons
   uint32_t* tables = reinterpret_cast<uint32_t*>(smem4);
   const uint32_t W = B + 2 * Tb;
   const uint32_t area = W * W;
-  uint32_t* xbuf = tables + kDevBlockWords;  // kTbExtWords per thread, interleaved
+  uint32_t* xbuf = tables + kDevStagedWords;  // kTbExtWords per thread, interleaved
   uint16_t* bufA = reinterpret_cast<uint16_t*>(xbuf + kTbExtWords * kTbThreads);
   uint16_t* bufB = bufA + 5 * area;
   __shared__ int skip;
@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(kTbThreads, 2) step_tb_kernel(StepArgs a, cons
   const size_t plane = size_t(Lx) * Ly;
   if (threadIdx.x == 0) skip = (*reinterpret_cast<volatile unsigned long long*>(fail) != ~0ull);
   const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
-  for (uint32_t i = threadIdx.x; i < kDevBlockWords / 4; i += blockDim.x) smem4[i] = g4[i];
+#pragma unroll 8
+  for (uint32_t i = threadIdx.x; i < kDevStagedWords / 4; i += blockDim.x) smem4[i] = g4[i];
   __syncthreads();
   if (skip) return;
 
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kTbThreads, 2) step_tb_kernel(StepArgs a, cons
 
 size_t step_tb_smem_bytes(uint32_t B, uint32_t Tb) {
   const size_t W = B + 2 * Tb;
-  return sizeof(uint32_t) * (kDevBlockWords + kTbExtWords * kTbThreads) + 2 * 5 * W * W * sizeof(uint16_t);
+  return sizeof(uint32_t) * (kDevStagedWords + kTbExtWords * kTbThreads) + 2 * 5 * W * W * sizeof(uint16_t);
 }
 
 cudaError_t prepare_step_tb_kernel(uint32_t B, uint32_t Tb) {

@@ -154,7 +154,8 @@ __device__ __forceinline__ bool vec_prologue(const StepArgs& a, uint4* smem4, co
   __shared__ int skip;
   if (threadIdx.x == 0) skip = (*reinterpret_cast<const volatile unsigned long long*>(fail) != ~0ull);
   const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
-  for (uint32_t i = threadIdx.x; i < kDevBlockWords / 4; i += blockDim.x) smem4[i] = g4[i];
+#pragma unroll 8
+  for (uint32_t i = threadIdx.x; i < kDevStagedWords / 4; i += blockDim.x) smem4[i] = g4[i];
   __syncthreads();
   return !skip;
 }
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kVecThreads, MINB)
   if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
 }
 
-constexpr size_t kVecSmem = sizeof(uint32_t) * kDevBlockWords;
+constexpr size_t kVecSmem = sizeof(uint32_t) * kDevStagedWords;
 constexpr int kNPT = 8;
 constexpr int kMinBlocks = 3;
 

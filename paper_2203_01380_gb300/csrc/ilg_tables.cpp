@@ -134,8 +134,9 @@ void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t P_
   }
 }
 
-// The device table block of a lattice: the two alias tables (binomial sampler) or
-// the particle boundaries.
+// The device table block of a lattice: the two alias tables (binomial sampler),
+// followed for D1Q3 / D2Q5 by the same two tables packed one word per column for
+// kernels short of shared memory; or the particle boundaries.
 void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis,
                        uint32_t* block) {
   std::fill(block, block + (Q == 9 ? kBlockWords9 : kBlockWords), 0u);
@@ -150,6 +151,15 @@ void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_res
   if (P_omega > 0 && P_omega < two32) build_alias_table(P_omega, al);
   if (P_rest > 0 && P_rest < two32) build_alias_table(P_rest, al + kAliasEntries);
   if (Q == 9 && P_axis > 0 && P_axis < two32) build_alias_table(P_axis, al + 2 * kAliasEntries);
+  if (Q == 9) return;
+  // packed entry of column j: (thr - j 2^26) << 6 | alias, or j for a full column
+  // (alias j); the draw then compares u's offset in its column, shifted up over six
+  // one bits, with the word
+  uint32_t* packed = block + kPackedOffset;
+  for (uint32_t i = 0; i < 2 * kAliasEntries; ++i) {
+    const uint32_t j = i % kAliasCols;
+    packed[i] = al[i].alias == j ? j : (((al[i].thr - (j << 26)) << 6) | al[i].alias);
+  }
 }
 
 double axis_share(double theta) {
