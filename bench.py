@@ -44,7 +44,7 @@ SMS = 152
 # DRAM bytes (read + write) of one 16384^2 launch of a step kernel, from the ncu
 # capture summarised in profiles/ (scaled from a 4096^2 launch by node count); only
 # kernels unchanged since their capture are listed
-TRAFFIC_BYTES_PER_LAUNCH = {}
+TRAFFIC_BYTES_PER_LAUNCH = {"seg8": 5.187e9}
 
 
 def peaks():
@@ -457,7 +457,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=inputs.LARGE_D2Q5["Lx"], help="lattice side (default 16384)")
+    ap.add_argument("--side-y", type=int, default=0, help="rows of the lattice (default: --side; profiling only)")
     ap.add_argument("--tsteps", type=int, default=inputs.LARGE_D2Q5["steps"], help="lattice steps per bench step")
+    ap.add_argument("--kernel", default="", choices=["", "vec8", "vec4", "node", "seg8"],
+                    help="fixed single-step kernel instead of the autotuner's choice (profiling: under ncu the "
+                         "tuner's timings are not the run's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip every measurement beyond the main workload")
@@ -470,7 +474,7 @@ def main():
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     cfg = {k: v for k, v in inputs.LARGE_D2Q5.items() if k != "steps"}
-    cfg.update(Lx=args.side, Ly=args.side)
+    cfg.update(Lx=args.side, Ly=args.side_y or args.side)
     cfg = rank_workload(cfg, rank)
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)
@@ -491,7 +495,11 @@ def main():
     lat = B.Lattice(**cfg, stream=stream)
     lat.init()
     nodes = cfg["Lx"] * cfg["Ly"]
-    tuning = lat.autotune(20)   # launch shape chosen by timing (outside the timed region)
+    if args.kernel:
+        lat.set_step_kernel(B.CONTEXT_CANDIDATES.index(args.kernel))
+        tuning = {"choice": args.kernel, "fixed": True}
+    else:
+        tuning = lat.autotune(20)   # launch shape chosen by timing (outside the timed region)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -568,7 +576,7 @@ def main():
         lat.set_temporal_blocking(0)
         if tb:
             extra["temporal_blocking"] = {"steps_per_launch": tb, "single_step_kernel": {"value": value, "unit": "GNUPS"},
-                                          "tile": "48 x 48 with a halo of depth nodes"}
+                                          "tile": "44 - 2 depth nodes per side, with a halo of depth nodes"}
         if "batched" in parts:
             extra["batched"] = measure_batched(torch, B, dev, args.batch_rings, args.batch_steps)
         if "lb" in parts:
