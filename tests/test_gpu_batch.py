@@ -46,6 +46,26 @@ def test_batch_init_and_run_match_oracle(B):
             assert np.array_equal(got, ref.run(ref.init(), 0, T)), (i, r)
 
 
+def test_batch_longest_rings_match_oracle(B):
+    """Rings at the length limit (10240 nodes, the ring and its copy in shared memory
+    beside the packed tables and 1024 threads' extension words) next to a short one,
+    through every block shape the autotuner times."""
+    reps = [dict(lattice=1, Lx=L, n0=n0, amp=8.0, mode_mx=1, omega_eff=w, seed=11, replica=i)
+            for i, (L, n0, w) in enumerate([(10240, 20.0, 1.5), (10233, 60.0, 0.8), (100, 10.0, 1.9)])]
+    with B.Batch(reps) as bat:
+        bat.init()
+        bat.run(6)
+        tun = bat.autotune(3)
+        assert all(v is not None for v in tun["ms_per_step"].values())
+        bat.run(4)
+        for i, r in enumerate(reps):
+            got, t = bat.get_state(i)
+            ref = O.Lattice(**r)
+            assert t == 10 and np.array_equal(got, ref.run(ref.init(), 0, 10)), i
+    with pytest.raises(B.IlgError):
+        B.Batch([dict(lattice=1, Lx=10241, seed=1)])
+
+
 def test_batch_mixed_samplers_match_oracle(B):
     """Rings with the particle sampler next to rings with the binomial sampler."""
     reps = [dict(lattice=1, Lx=L, n0=n0, amp=0.0, omega_eff=w, seed=8, replica=i, sampler=i % 2)
