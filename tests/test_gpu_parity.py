@@ -237,8 +237,10 @@ def test_checkpoint_resume(B):
 
 def test_large_d2q5_light_cone_full_size(B):
     """16384^2, mean 10 per velocity, omega_eff 1.8, 500 steps (the throughput
-    workload, same kernels and launch shape): a 12 x 12 window at t = 500 from
-    the oracle's own initial state of its light cone; plus exact mass."""
+    workload, same kernels and launch shape): 12 x 12 windows at t = 500 from the
+    oracle's own initial state of their light cones, one across the periodic seam of
+    the rows and one across the middle of the rows (where the default kernel's two
+    8192-node segments of a row meet); plus exact mass."""
     cfg = {k: v for k, v in inputs.LARGE_D2Q5.items() if k != "steps"}
     steps = inputs.LARGE_D2Q5["steps"]
     x0, y0, w = 16384 - 5, 9000, 12
@@ -251,9 +253,10 @@ def test_large_d2q5_light_cone_full_size(B):
         lat.get_state(state)
     assert obs["mass"] == m0 and obs["t"] == steps
     ref = O.Lattice(**cfg)
-    win = ref.window(x0, y0, w, w, steps)
-    xs = [(x0 + i) % 16384 for i in range(w)]
-    assert np.array_equal(state[:, y0:y0 + w][:, :, xs], win)
+    for x0, y0 in ((x0, y0), (8192 - 6, 3000)):
+        win = ref.window(x0, y0, w, w, steps)
+        xs = [(x0 + i) % 16384 for i in range(w)]
+        assert np.array_equal(state[:, y0:y0 + w][:, :, xs], win), (x0, y0)
 
 
 # ---------------------------------------------------------------- edge cases
