@@ -24,7 +24,7 @@
  *     ilg_last_error() describes the last failure on a context.
  *   - "stream" is a cudaStream_t (NULL = the legacy default stream).  Kernels of a
  *     context run on its stream; calls that return host data synchronise it.
- *   - Random numbers: Philox4x32-10, key = seed, counter = (node x + Lx*y, step t,
+ *   - Random numbers: Philox4x32-10, key = seed, counter = (step t, node x + Lx*y,
  *     replica, purpose tag and block).  Results do not depend on launch shape,
  *     stream, batching or placement.
  */
