@@ -326,6 +326,32 @@ def measure_particle(torch, B, dev, side):
             "kernel": "step_kernel<5> (general path, one Philox word per particle)"}
 
 
+def measure_sweep(torch, B, dev):
+    """The omega sweep workload (D2Q5 1024^2, mean 50 per velocity + a sine of amplitude
+    20), each omega_eff autotuned and timed over 200 steps: at these occupations most
+    nodes need the general collision (chunked binomials, extension words)."""
+    out = {}
+    st = torch.cuda.Stream(dev)
+    T = 200
+    for c in inputs.SWEEP_D2Q5:
+        cfg = {k: v for k, v in c.items() if k != "steps"}
+        with B.Lattice(**cfg, stream=st) as lat:
+            lat.init()
+            tun = lat.autotune(10)
+            lat.step(10)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(st)
+            lat.step(T)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / T
+        out[str(c["omega_eff"])] = {"value": cfg["Lx"] * cfg["Ly"] / (ms / 1e3) / 1e9, "unit": "GNUPS",
+                                    "ms_per_step": ms, "kernel": tun["choice"]}
+    return {"workload": f"sweep_d2q5: D2Q5 1024x1024, Poisson mean 50 per velocity + sine amplitude 20, "
+                        f"{T} steps per omega_eff", "omega_eff": out}
+
+
 def measure_d2q9(torch, B, dev, side):
     """The D2Q9 lattice (9 velocities, product weights) on the main workload's size."""
     cfg = {k: v for k, v in inputs.LARGE_D2Q9.items() if k != "steps"}
@@ -465,7 +491,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip every measurement beyond the main workload")
-    ap.add_argument("--extra", default="tb,batched,lb,ensemble,particle,d2q9,serving",
+    ap.add_argument("--extra", default="tb,batched,lb,ensemble,particle,d2q9,sweep,serving",
                     help="comma-separated measurements beyond the main workload")
     ap.add_argument("--lb-side", type=int, default=0, help="side of the lattice Boltzmann workload (default 16384)")
     ap.add_argument("--batch-rings", type=int, default=4096, help="rings of the batched workload (profiling only)")
@@ -587,6 +613,8 @@ def main():
             extra["particle_sampler"] = measure_particle(torch, B, dev, args.side)
         if "d2q9" in parts:
             extra["d2q9"] = measure_d2q9(torch, B, dev, args.side)
+        if "sweep" in parts:
+            extra["sweep"] = measure_sweep(torch, B, dev)
         if "serving" in parts:
             extra["serving"] = measure_serving(B, args.serve_requests)
 

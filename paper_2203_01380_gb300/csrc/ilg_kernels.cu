@@ -11,8 +11,9 @@ namespace ilg {
 // --------------------------------------------------------------------------
 // step: one thread per node, any extent.  Loads the Q occupations of its node,
 // flips, collides and scatters n'_i to the neighbour x + v_i (periodic).
-// The table block (CDF rows and guide cells) is staged in shared memory once per
-// block.  A block returns without work when an earlier launch recorded an
+// The lattice's two alias tables, packed one word per column, are staged in shared
+// memory once per block, beside 24 extension words per thread for the general
+// collision.  A block returns without work when an earlier launch recorded an
 // overflow.
 // --------------------------------------------------------------------------
 constexpr int kStepThreads = 256;
