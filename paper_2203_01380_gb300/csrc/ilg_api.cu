@@ -395,7 +395,7 @@ cudaError_t launch_single(const ilg_ctx* c, int kind, const StepArgs& a, const u
     const uint64_t blocks = (step_seg_units(c->p.Lx, c->p.Ly) + 7) / 8, cap = vec_warps(c) / 8;
     return launch_step_seg(c->Q, a, in, out, uint32_t(t), fail_word, int(blocks < cap ? blocks : cap), c->stream);
   }
-  return launch_step(c->Q, a, in, out, uint32_t(t), fail_word, step_grid(c, 3), c->stream);
+  return launch_step(c->Q, a, in, out, uint32_t(t), fail_word, step_grid(c, 4), c->stream);
 }
 
 int tb_grid(const ilg_ctx* c, uint32_t depth) {

@@ -24,7 +24,7 @@ constexpr uint32_t kDevTagStep = 1u << 24;
 constexpr uint32_t kDevTagExt = 2u << 24;
 constexpr uint32_t kDevTagInit = 3u << 24;
 constexpr uint32_t kDevTagParticle = 4u << 24;
-constexpr int kExtWords = 24;        // extension words per thread held in shared memory
+constexpr int kExtWords = 20;        // extension words per thread held in shared memory
 
 // How a probability P/2^32 is drawn: never (P = 0), by table (0 < P < 2^32),
 // always (P = 2^32).

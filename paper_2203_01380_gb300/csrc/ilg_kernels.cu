@@ -12,14 +12,17 @@ namespace ilg {
 // step: one thread per node, any extent.  Loads the Q occupations of its node,
 // flips, collides and scatters n'_i to the neighbour x + v_i (periodic).
 // The lattice's two alias tables, packed one word per column, are staged in shared
-// memory once per block, beside 24 extension words per thread for the general
+// memory once per block, beside 20 extension words per thread for the general
 // collision.  A block returns without work when an earlier launch recorded an
 // overflow.
 // --------------------------------------------------------------------------
 constexpr int kStepThreads = 256;
 
+// (four blocks per SM: 32 KB of packed tables and 20 KB of extension words each)
+constexpr int kStepBlocksPerSm = 4;
+
 template <int Q>
-__global__ void __launch_bounds__(kStepThreads, 3) step_kernel(StepArgs a, const uint16_t* __restrict__ in,
+__global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(StepArgs a, const uint16_t* __restrict__ in,
                                                       uint16_t* __restrict__ out, uint32_t t,
                                                       unsigned long long* __restrict__ fail) {
   extern __shared__ uint4 smem4[];

@@ -28,7 +28,7 @@ struct LatDesc {
   const uint32_t* tables;  // kDevBlockWords words
 };
 
-constexpr int kMultiBlocksPerSm = 3;   // resident blocks per SM (the kernel's launch bounds)
+constexpr int kMultiBlocksPerSm = 4;   // resident blocks per SM (the kernel's launch bounds)
 
 struct WorkItem {
   uint32_t lattice, node0, node1;  // nodes [node0, node1) of the lattice, row-major
