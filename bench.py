@@ -444,6 +444,15 @@ def measure_serving(B, n_requests=200):
                             "speedup": plain_s / served_s}}
 
 
+def main_config(cfg, T, nmodes, world):
+    """The `config` object of both arms' lines: the main workload."""
+    return {"workload": f"large_d2q5: D2Q5 {cfg['Lx']}x{cfg['Ly']}, Poisson mean 10 per velocity, "
+                        f"omega_eff 1.8, {T} steps + observables (S(k), m=1..{nmodes}) per bench step",
+            "Lx": cfg["Lx"], "Ly": cfg["Ly"], "steps_per_bench_step": T, "modes": nmodes,
+            "parallelism": f"replicas x{world}",
+            "l2": "no flush: the double-buffered state is larger than L2"}
+
+
 def run_reference(args, cfg, world, rank):
     """The oracle as the reference arm: every step runs one light-cone window per host
     core, in parallel processes (spawned), on the same workload."""
@@ -470,7 +479,7 @@ def run_reference(args, cfg, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GNUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
-            "data": "synthetic", "config": {"workload": "large_d2q5 (sampled)", "Lx": cfg["Lx"], "Ly": cfg["Ly"]},
+            "data": "synthetic", "config": main_config(cfg, args.tsteps, len(inputs.LARGE_MODES), world),
             "cpu_baseline": {"value": v, "unit": "GNUPS", "cores": n, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "GNUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -640,11 +649,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "GNUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-            "config": {"workload": f"large_d2q5: D2Q5 {cfg['Lx']}x{cfg['Ly']}, Poisson mean 10 per velocity, "
-                                   f"omega_eff 1.8, {T} steps + observables (S(k), m=1..64) per bench step",
-                       "Lx": cfg["Lx"], "Ly": cfg["Ly"], "steps_per_bench_step": T, "modes": len(modes),
-                       "parallelism": f"replicas x{world}",
-                       "l2": "no flush: the double-buffered state is larger than L2"},
+            "config": main_config(cfg, T, len(modes), world),
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": launches,
