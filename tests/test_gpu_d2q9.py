@@ -1,6 +1,7 @@
 """D2Q9 lattices (ilg_create with ILG_D2Q9, and the comparator) against the oracle:
 initial states, states after T steps with both samplers (every flip / omega* regime,
-occupations far above the fast path, odd extents), observables, overflow rollback,
+occupations far above the fast path, odd extents and even ones, which take two nodes
+per thread), observables, overflow rollback,
 the 16384^2 workload through a light-cone window, and the replica mean against the
 lattice Boltzmann comparator."""
 import numpy as np
@@ -41,6 +42,10 @@ STEP_CASES = [
     (33, 17, 1.4, 0.2, 70.0, 3, 0),      # general path: chunks, extension words
     (31, 19, 1.6, 1 / 3, 8.0, 2, 1),     # particle sampler
     (40, 12, 0.5, 0.6, 15.0, 0, 1),
+    # even rows take two nodes per thread: the pair at the row's end wraps to x = 0
+    (4, 5, 1.7, 1 / 3, 30.0, 2, 0),
+    (6, 3, 0.9, 0.4, 70.0, 1, 0),
+    (34, 7, 1.2, 1 / 3, 11.0, 0, 1),
 ]
 
 
