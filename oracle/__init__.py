@@ -327,9 +327,11 @@ def trig(r: int, L: int):
 
 
 def project_exact(sums: np.ndarray, L: int, m: int, M: int):
-    """Re, Im of sum_x e^{-2 pi i m x / L} (L*sums[x] - M) / L, exactly from the
-    double sines/cosines, rounded once.  Returns (re, im, scale) where scale =
-    sum_x |L*sums[x] - M| / L bounds the condition of both sums."""
+    """Projections of Sec. V's measured profile on mode m, with D(x) = L*sums[x] - M:
+    re = sum_x cos(2 pi r / L) D(x) / L and im = sum_x sin(2 pi r / L) D(x) / L,
+    r = (m x) mod L, evaluated exactly from the double cosines and sines and rounded
+    once.  Returns (re, im, scale) where scale = sum_x |D(x)| / L bounds the
+    condition of both sums."""
     mm = m % L
     re = Fraction(0)
     im = Fraction(0)
