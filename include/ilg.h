@@ -149,6 +149,14 @@ ilg_status ilg_set_temporal_blocking(ilg_ctx* ctx, uint32_t depth);
  *   candidate 5  8-node vectors in warp segments: each warp walks 8192 nodes of a row,
  *                neighbours exchanged by shuffles, no block barrier (the default
  *                where the lattice has two segments per resident warp)
+ *   candidate 6  4-node vectors in warp segments (rows a multiple of 4; both collision
+ *                probabilities strictly between 0 and 1): every warp an equal share
+ *                of the lattice's vectors, the next tile's occupations copied into
+ *                shared memory while the current one collides, the flip a
+ *                compile-time plane order, the fast collision branch-free, the
+ *                values crossing a segment's ends written by the warp that computes
+ *                them (no node computed twice); one block of 768 threads per SM
+ *   candidate 7  as 6 with one block of 512 threads per SM
  * Candidates that do not apply (row length, D2Q9, occupations that need the general
  * collision) are skipped (ms_per_step < 0).  A choice that stops applying after
  * ilg_set_state (e.g. occupations rise) falls back to the default.  trial_steps:
@@ -164,7 +172,7 @@ typedef struct {
 } ilg_tuning;
 
 ilg_status ilg_autotune(ilg_ctx* ctx, uint32_t trial_steps, ilg_tuning* out);
-/* Set the single-step kernel by hand: candidate 0, 1, 2 or 5 as above, -1 the default.
+/* Set the single-step kernel by hand: candidate 0, 1, 2, 5, 6 or 7 as above, -1 the default.
  * A candidate that does not apply to the current state falls back to the default;
  * results are the same bits either way. */
 ilg_status ilg_set_step_kernel(ilg_ctx* ctx, int32_t candidate);
@@ -225,6 +233,15 @@ ilg_status ilg_batch_init(ilg_batch* b);
 ilg_status ilg_batch_set_state(ilg_batch* b, uint32_t i, const uint16_t* host, size_t n, uint64_t t);
 ilg_status ilg_batch_get_state(ilg_batch* b, uint32_t i, uint16_t* host, size_t n, uint64_t* t);
 ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record);
+/* As ilg_batch_run, and the state of every ring after every step (Sec. V's profile
+ * followed in time) goes to state_record (host array of T * sum_i 3 L_i uint16, or
+ * NULL): ring i's record starts at T * o_i, o_i = sum_{r < i} 3 L_r, and holds its
+ * state after step s (planes rest, +1, -1 as ilg_batch_get_state) at T * o_i + 3 L_i s.
+ * A ring that stopped on overflow has no record after the step it stopped before.
+ * The device copy of the record is allocated by the call (ILG_E_OOM if it does not
+ * fit) and kept for later calls. */
+ilg_status ilg_batch_run_record(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record,
+                                uint16_t* state_record);
 ilg_status ilg_batch_observables(ilg_batch* b, int32_t mode, uint64_t* mass, double* amp);
 ilg_status ilg_batch_ensemble(ilg_batch* b, uint32_t T, int32_t mode, double* stats, double* record);
 /* Batch autotuner: times the block shapes 256, 512 and 1024 threads (candidates 0-2;
@@ -323,6 +340,12 @@ typedef struct ilg_lb ilg_lb;
 ilg_status ilg_lb_create(const ilg_lb_params* params, void* stream, ilg_lb** out);
 ilg_status ilg_lb_destroy(ilg_lb* lb);
 const char* ilg_lb_last_error(const ilg_lb* lb);
+/* The comparator's rates for the lattice gas with parameter omega_eff (Sec. IV, Eq.
+ * omegaj): omega_eff > 1 (the flip on, collision fraction omega* = 2 - omega_eff)
+ * gives omega_j = omega_eff for the current and omega = omega* for the other
+ * non-conserved moments; omega_eff <= 1 gives omega_j = omega = omega_eff.  Host
+ * only.  ILG_E_INVALID unless omega_eff lies in (0, 2] and both outputs are non-NULL. */
+ilg_status ilg_lb_rates(double omega_eff, double* omega_j, double* omega);
 /* f := lambda (the gas's Poisson means, Sec. V), t := 0. */
 ilg_status ilg_lb_init(ilg_lb* lb);
 /* Copy a state in or out (host arrays of n = Q*Lx*Ly doubles); synchronous. */
@@ -341,9 +364,9 @@ ilg_status ilg_lb_observables(ilg_lb* lb, const int32_t* modes, uint32_t nmodes,
 
 /* Observables of a state in caller-owned device memory, allocating nothing (the
  * paper has no counterpart; this serves callers that cannot allocate device memory
- * when they need the numbers: code running while a stream is captured into a CUDA
- * graph, real-time loops that must not take the allocator's locks or its implicit
- * synchronisation, hosts whose device memory all belongs to their own pool).
+ * when they need the numbers: applications whose device memory all belongs to their
+ * own pool, so that cudaMalloc would fail, and real-time loops that must not wait on
+ * the allocator's locks or on the device-wide synchronisation of freeing memory).
  *   lattice, Lx, Ly  as in ilg_params (Ly taken as 1 for D1Q3); Lx, Ly <= 32768
  *   state            device array, Q*Lx*Ly uint16 in the plane layout above (read only)
  *   modes, nmodes    host array of nmodes <= 256 axis modes (mx, my), as ilg_observables
@@ -378,6 +401,30 @@ ilg_status ilg_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t 
 ilg_status ilg_binomial_table(uint64_t P, uint32_t* out);
 ilg_status ilg_alias_table(uint64_t P, uint32_t* thr, uint32_t* alias);
 ilg_status ilg_poisson_table(double lambda, uint32_t* out, uint32_t cap, uint32_t* K);
+
+/* Integer throughput of the GPU, measured (the paper has no counterpart: these are
+ * the denominators of the step kernels' integer roofline, whose random numbers and
+ * table draws bound the step).  Kernels of fixed length on registers only, enough
+ * warps on every SM to hide fixed latencies, eight independent chains per thread,
+ * timed with CUDA events on `stream` over a region of `seconds` (0.05 .. 10) after a
+ * calibration.  kind:
+ *   0  Philox4x32-10 blocks per second (the generator of every step, with the
+ *      step's counter layout: a launch-wide word, a per-thread word, constants)
+ *   1  3-input logic (lop3) lane-operations per second
+ *   2  32-bit multiply-add lane-operations per second
+ *   3  32x32 -> 64-bit multiply-add lane-operations per second
+ *   4  lane-operations per second of an even mix of kinds 1 and 2
+ * *rate receives the figure, *ms (may be NULL) the timed region.  Synchronous.
+ * ILG_E_INVALID for a bad kind or length (message in ilg_last_error(NULL)). */
+ilg_status ilg_int_peak(int32_t kind, double seconds, void* stream, double* rate, double* ms);
+
+/* Failure injection for tests of the error paths (the paper has no counterpart).
+ * After `after` more successful device allocations made by the library (contexts,
+ * batches, the server's arena and buffers, the comparator, scratch), the next one
+ * reports failure without calling the allocator, so that call returns ILG_E_OOM
+ * having released what it had allocated; then injection is off again.  after < 0
+ * switches it off.  Process-wide; host only; always ILG_OK. */
+ilg_status ilg_inject_alloc_failure(int64_t after);
 
 #ifdef __cplusplus
 }

@@ -74,6 +74,7 @@ _lib.ilg_batch_init.argtypes = [_vp]
 _lib.ilg_batch_set_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t, ctypes.c_uint64]
 _lib.ilg_batch_get_state.argtypes = [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]
 _lib.ilg_batch_run.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp]
+_lib.ilg_batch_run_record.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp, _vp]
 _lib.ilg_batch_observables.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
 _lib.ilg_batch_ensemble.argtypes = [_vp, ctypes.c_uint32, ctypes.c_int32, _vp, _vp]
 class Tuning(ctypes.Structure):
@@ -81,7 +82,7 @@ class Tuning(ctypes.Structure):
                 ("n", ctypes.c_uint32), ("ms_per_step", ctypes.c_double * 8)]
 
 
-CONTEXT_CANDIDATES = ("vec8", "vec4", "node", "tb2", "tb4", "seg8")
+CONTEXT_CANDIDATES = ("vec8", "vec4", "node", "tb2", "tb4", "seg8", "warp768", "warp512")
 BATCH_CANDIDATES = ("threads256", "threads512", "threads1024")
 
 
@@ -120,10 +121,13 @@ _lib.ilg_philox.argtypes = [_u32p, ctypes.c_uint64, _u32p, ctypes.c_size_t, _vp]
 _lib.ilg_binomial_table.argtypes = [ctypes.c_uint64, _u32p]
 _lib.ilg_alias_table.argtypes = [ctypes.c_uint64, _u32p, _u32p]
 _lib.ilg_poisson_table.argtypes = [ctypes.c_double, _u32p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+_lib.ilg_int_peak.argtypes = [ctypes.c_int32, ctypes.c_double, _vp, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)]
 for _f in ("ilg_set_temporal_blocking", "ilg_create", "ilg_destroy", "ilg_init", "ilg_set_state", "ilg_set_state_device", "ilg_get_state",
            "ilg_get_state_device", "ilg_step", "ilg_observables", "ilg_philox", "ilg_binomial_table",
-           "ilg_alias_table", "ilg_poisson_table", "ilg_observables_noalloc", "ilg_batch_create", "ilg_batch_destroy",
-           "ilg_batch_init", "ilg_batch_set_state", "ilg_batch_get_state", "ilg_batch_run", "ilg_batch_observables",
+           "ilg_alias_table", "ilg_poisson_table", "ilg_int_peak", "ilg_observables_noalloc", "ilg_batch_create", "ilg_batch_destroy",
+           "ilg_batch_init", "ilg_batch_set_state", "ilg_batch_get_state", "ilg_batch_run", "ilg_batch_run_record",
+           "ilg_batch_observables",
            "ilg_batch_ensemble",
            "ilg_server_create", "ilg_server_submit", "ilg_server_poll", "ilg_server_wait_idle", "ilg_server_stats",
            "ilg_server_destroy", "ilg_server_set_policy"):
@@ -232,7 +236,8 @@ class Lattice:
 
     def set_step_kernel(self, candidate: int):
         """ilg_set_step_kernel: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, 5 warp
-        segments of 8-node vectors, -1 default."""
+        segments of 8-node vectors, 6 / 7 warp segments of 4-node vectors (one block of 768 /
+        512 threads per SM), -1 default."""
         _check(_lib.ilg_set_step_kernel(self._h, int(candidate)), self._h)
 
     def set_temporal_blocking(self, depth: int):
@@ -305,6 +310,18 @@ class Batch:
         self._check(_lib.ilg_batch_run(self._h, int(T), int(record_mode or 0),
                                        rec.ctypes.data if rec is not None else None))
         return rec
+
+    def run_record(self, T, record_mode=1):
+        """ilg_batch_run_record: T steps with the amplitude of record_mode and the state of
+        every ring after every step; returns (amp (n, T), [per ring (T, 3, 1, L) states])."""
+        amp = np.zeros((self.n, T))
+        states = np.zeros(T * 3 * sum(self.L), dtype=np.uint16)
+        self._check(_lib.ilg_batch_run_record(self._h, int(T), int(record_mode), amp.ctypes.data, states.ctypes.data))
+        out, off = [], 0
+        for L in self.L:
+            out.append(states[off:off + T * 3 * L].reshape(T, 3, 1, L))
+            off += T * 3 * L
+        return amp, out
 
     def observables(self, mode=1):
         mass = np.zeros(self.n, dtype=np.uint64)
@@ -423,9 +440,15 @@ for _f in ("ilg_lb_create", "ilg_lb_destroy", "ilg_lb_init", "ilg_lb_set_state",
     getattr(_lib, _f).restype = ctypes.c_int
 
 
+_lib.ilg_lb_rates.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+_lib.ilg_lb_rates.restype = ctypes.c_int
+
+
 def lb_rates(omega_eff: float):
-    """(omega_j, omega) of the lattice gas with parameter omega_eff (the flip above 1)."""
-    return (omega_eff, 2.0 - omega_eff) if omega_eff > 1.0 else (omega_eff, omega_eff)
+    """ilg_lb_rates: (omega_j, omega) of the comparator for the lattice gas's omega_eff."""
+    oj, om = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ilg_lb_rates(float(omega_eff), ctypes.byref(oj), ctypes.byref(om)))
+    return oj.value, om.value
 
 
 class LB:
@@ -533,3 +556,24 @@ def poisson_table(lam: float, cap: int = 4096) -> np.ndarray:
     K = ctypes.c_uint32()
     _check(_lib.ilg_poisson_table(float(lam), out, cap, ctypes.byref(K)))
     return out[:K.value].copy()
+
+
+INT_PEAK_KINDS = ("philox_blocks", "lop3", "imad", "imad_wide", "lop3_imad_mix")
+
+
+def int_peak(kind: int, seconds: float = 1.0, stream=None) -> dict:
+    """ilg_int_peak: measured integer throughput of the GPU (see include/ilg.h)."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ilg_int_peak(int(kind), float(seconds), _vp(stream_handle(stream)), ctypes.byref(rate),
+                             ctypes.byref(ms)))
+    return dict(kind=INT_PEAK_KINDS[kind], rate=rate.value, ms=ms.value)
+
+
+_lib.ilg_inject_alloc_failure.argtypes = [ctypes.c_int64]
+_lib.ilg_inject_alloc_failure.restype = ctypes.c_int
+
+
+def inject_alloc_failure(after: int):
+    """ilg_inject_alloc_failure: the library's (after+1)-th next device allocation fails;
+    after < 0 switches injection off."""
+    _check(_lib.ilg_inject_alloc_failure(int(after)))

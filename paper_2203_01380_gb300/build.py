@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libilg.so")
-SOURCES = ["ilg_api.cu", "ilg_kernels.cu", "ilg_step_vec.cu", "ilg_step_tb.cu", "ilg_noalloc.cu", "ilg_batch.cu", "ilg_batch_api.cu", "ilg_multi.cu", "ilg_server.cu", "ilg_lb.cu", "ilg_d2q9.cu", "ilg_tables.cpp"]
+SOURCES = ["ilg_api.cu", "ilg_kernels.cu", "ilg_step_vec.cu", "ilg_step_warp.cu", "ilg_step_tb.cu", "ilg_noalloc.cu", "ilg_batch.cu", "ilg_batch_api.cu", "ilg_multi.cu", "ilg_server.cu", "ilg_lb.cu", "ilg_d2q9.cu", "ilg_peak.cu", "ilg_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",
                 "-Xptxas", "-O3"]
@@ -64,7 +64,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
                 print(msg, file=sys.stderr)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
+        run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

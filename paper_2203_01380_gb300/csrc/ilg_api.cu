@@ -204,16 +204,16 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
   if (e != cudaSuccess) return bail(e, "cudaDeviceGetAttribute");
   const size_t state_bytes = sizeof(uint16_t) * c->nodes * c->Q;
   for (int b = 0; b < 2; ++b) {
-    e = cudaMalloc(&c->buf[b], state_bytes);
+    e = dev_alloc(&c->buf[b], state_bytes);
     if (e != cudaSuccess) return bail(e, "cudaMalloc state");
   }
   static_assert(kBlockWords == kDevBlockWords && kBlockWords9 == kDevBlockWords9, "table block layout");
   const size_t block_words = c->Q == 9 ? kBlockWords9 : kBlockWords;
-  if ((e = cudaMalloc(&c->d_tables, sizeof(uint32_t) * block_words)) != cudaSuccess) return bail(e, "cudaMalloc tables");
-  if ((e = cudaMalloc(&c->d_fail, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc flag");
-  if ((e = cudaMalloc(&c->d_col, sizeof(unsigned long long) * c->p.Lx)) != cudaSuccess) return bail(e, "cudaMalloc sums");
-  if ((e = cudaMalloc(&c->d_row, sizeof(unsigned long long) * c->p.Ly)) != cudaSuccess) return bail(e, "cudaMalloc sums");
-  if ((e = cudaMalloc(&c->d_mass, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc mass");
+  if ((e = dev_alloc(&c->d_tables, sizeof(uint32_t) * block_words)) != cudaSuccess) return bail(e, "cudaMalloc tables");
+  if ((e = dev_alloc(&c->d_fail, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc flag");
+  if ((e = dev_alloc(&c->d_col, sizeof(unsigned long long) * c->p.Lx)) != cudaSuccess) return bail(e, "cudaMalloc sums");
+  if ((e = dev_alloc(&c->d_row, sizeof(unsigned long long) * c->p.Ly)) != cudaSuccess) return bail(e, "cudaMalloc sums");
+  if ((e = dev_alloc(&c->d_mass, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc mass");
   if ((e = cudaMallocHost(&c->h_word, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMallocHost");
 
   std::vector<uint32_t> tables(block_words, 0u);
@@ -221,6 +221,7 @@ ilg_status ilg_create(const ilg_params* params, void* stream, ilg_ctx** out) {
   if ((e = prepare_step9_kernel()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   if ((e = prepare_step_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   if ((e = prepare_step_vec_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
+  if ((e = prepare_step_warp_kernels()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   e = cudaMemcpyAsync(c->d_tables, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return bail(e, "copy tables");
   e = cudaMemsetAsync(c->d_fail, 0xFF, sizeof(unsigned long long), c->stream);
@@ -251,9 +252,9 @@ ilg_status ilg_init(ilg_ctx* c) {
     cudaFree(d_tab);
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&d_off, sizeof(uint32_t) * it.offset.size())) != cudaSuccess ||
-      (e = cudaMalloc(&d_cnt, sizeof(uint32_t) * it.count.size())) != cudaSuccess ||
-      (e = cudaMalloc(&d_tab, sizeof(uint32_t) * it.table.size())) != cudaSuccess) {
+  if ((e = dev_alloc(&d_off, sizeof(uint32_t) * it.offset.size())) != cudaSuccess ||
+      (e = dev_alloc(&d_cnt, sizeof(uint32_t) * it.count.size())) != cudaSuccess ||
+      (e = dev_alloc(&d_tab, sizeof(uint32_t) * it.table.size())) != cudaSuccess) {
     cleanup();
     return cuda_fail(c, e, "cudaMalloc init tables");
   }
@@ -356,13 +357,19 @@ namespace {
 
 // Single-step kernels, numbered as the autotuner's candidates (3 and 4 are the
 // temporal-blocking depths).
-enum : int { kKernelVec8 = 0, kKernelVec4 = 1, kKernelNode = 2, kKernelSeg = 5 };
+enum : int { kKernelVec8 = 0, kKernelVec4 = 1, kKernelNode = 2, kKernelSeg = 5, kKernelWarp768 = 6, kKernelWarp512 = 7 };
+constexpr int kCandidates = 8;
 
-bool is_single_step(int cand) { return cand <= kKernelNode || cand == kKernelSeg; }
+bool is_single_step(int cand) { return cand <= kKernelNode || (cand >= kKernelSeg && cand < kCandidates); }
 
 bool kernel_applies(const ilg_ctx* c, const StepArgs& a, int kind) {
   if (kind == kKernelNode) return true;
   if (c->Q == 9 || a.general) return false;  // D2Q9 and the general path run node-parallel
+  if (kind == kKernelWarp768 || kind == kKernelWarp512) {
+    // whole vectors per row; the fast collision draws both probabilities through tables
+    return c->p.Lx % step_warp_width(kind == kKernelWarp512 ? 1 : 0) == 0 && a.omega_mode == kTable &&
+           a.rest_mode == kTable;
+  }
   return c->p.Lx % (kind == kKernelVec4 ? 4u : 8u) == 0;
 }
 
@@ -381,7 +388,9 @@ int pick_kernel(const ilg_ctx* c, const StepArgs& a) {
 cudaError_t launch_single(const ilg_ctx* c, int kind, const StepArgs& a, const uint16_t* in, uint16_t* out,
                           uint64_t t, unsigned long long* fail_word) {
   if (c->Q == 9) {
-    const size_t blocks = (c->nodes + step9_threads() - 1) / step9_threads();
+    // rows of even length run two neighbouring nodes per thread (launch_step9)
+    const size_t work = c->p.Lx % 2 == 0 ? c->nodes / 2 : c->nodes;
+    const size_t blocks = (work + step9_threads() - 1) / step9_threads();
     const size_t cap = size_t(c->sms) * step9_blocks_per_sm();
     return launch_step9(a, in, out, uint32_t(t), fail_word, int(blocks < cap ? blocks : cap), c->stream);
   }
@@ -394,6 +403,12 @@ cudaError_t launch_single(const ilg_ctx* c, int kind, const StepArgs& a, const u
   if (kind == kKernelSeg) {
     const uint64_t blocks = (step_seg_units(c->p.Lx, c->p.Ly) + 7) / 8, cap = vec_warps(c) / 8;
     return launch_step_seg(c->Q, a, in, out, uint32_t(t), fail_word, int(blocks < cap ? blocks : cap), c->stream);
+  }
+  if (kind == kKernelWarp768 || kind == kKernelWarp512) {
+    const int shape = kind == kKernelWarp512 ? 1 : 0;
+    const uint32_t Ly = c->Q == 3 ? 1u : c->p.Ly;
+    return launch_step_warp(c->Q, shape, a, in, out, uint32_t(t), fail_word,
+                            int(step_warp_grid(c->p.Lx, Ly, uint32_t(c->sms), shape)), c->stream);
   }
   return launch_step(c->Q, a, in, out, uint32_t(t), fail_word, step_grid(c, 4), c->stream);
 }
@@ -408,6 +423,7 @@ int tb_grid(const ilg_ctx* c, uint32_t depth) {
 
 ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
   if (!c) return ILG_E_INVALID;
+  NvtxRange nvtx("ilg_step");
   if (!c->has_state) return fail(c, ILG_E_STATE, "no state: call ilg_init or ilg_set_state first");
   if (c->t + T >= (uint64_t(1) << 32)) return fail(c, ILG_E_INVALID, "step counter would reach 2^32");
   if (T == 0) return ILG_OK;
@@ -465,7 +481,7 @@ ilg_status ilg_step(ilg_ctx* c, uint32_t T) {
 ilg_status ilg_set_step_kernel(ilg_ctx* c, int32_t candidate) {
   if (!c) return ILG_E_INVALID;
   if (candidate < -1 || (candidate >= 0 && !is_single_step(candidate)))
-    return fail(c, ILG_E_INVALID, "candidate must be -1, 0, 1, 2 or 5");
+    return fail(c, ILG_E_INVALID, "candidate must be -1, 0, 1, 2, 5, 6 or 7");
   c->kernel_choice = candidate;
   return ILG_OK;
 }
@@ -491,9 +507,9 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   };
-  cudaError_t e = cudaMalloc(&s[0], bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&s[1], bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&fw, sizeof(unsigned long long));
+  cudaError_t e = dev_alloc(&s[0], bytes);
+  if (e == cudaSuccess) e = dev_alloc(&s[1], bytes);
+  if (e == cudaSuccess) e = dev_alloc(&fw, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s[0], c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -502,9 +518,10 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
     return cuda_fail(c, e, "autotune scratch");
   }
   // candidates: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, 3 / 4 temporal
-  // blocking of depth 2 / 4 (D2Q5), 5 warp segments of 8-node vectors
+  // blocking of depth 2 / 4 (D2Q5), 5 warp segments of 8-node vectors, 6 / 7 warp
+  // segments of 4-node vectors in one block of 768 / 512 threads per SM
   ilg_tuning res{};
-  res.n = 6;
+  res.n = kCandidates;
   for (int k = 0; k < 8; ++k) res.ms_per_step[k] = -1.0;
   auto trial = [&](int cand, double* ms_per_step) -> cudaError_t {
     const uint32_t depth = cand == 3 ? 2u : (cand == 4 ? 4u : 1u);
@@ -532,7 +549,7 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
     if (r == cudaSuccess && *c->h_word == ~0ull) *ms_per_step = double(ms) / (double(launches) * depth);
     return r;
   };
-  for (int cand = 0; cand < 6 && e == cudaSuccess; ++cand) {
+  for (int cand = 0; cand < kCandidates && e == cudaSuccess; ++cand) {
     if (is_single_step(cand) && !kernel_applies(c, a, cand)) continue;
     if (is_single_step(cand) && c->Q == 9 && cand != kKernelNode) continue;
     if (!is_single_step(cand)) {
@@ -545,13 +562,13 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
   release();
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune trial");
   int best = -1;
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < kCandidates; ++k)
     if (res.ms_per_step[k] >= 0.0 && (best < 0 || res.ms_per_step[k] < res.ms_per_step[best])) best = k;
   if (best < 0) return fail(c, ILG_E_OVERFLOW, "every trial overflowed: no choice made");
   if (!is_single_step(best)) {
     // temporal blocking; the remaining single steps take the fastest single-step kernel
     int single = -1;
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < kCandidates; ++k)
       if (is_single_step(k) && res.ms_per_step[k] >= 0.0 &&
           (single < 0 || res.ms_per_step[k] < res.ms_per_step[single]))
         single = k;
@@ -573,6 +590,7 @@ ilg_status ilg_observables(ilg_ctx* c, const int32_t* modes, uint32_t nmodes, ui
                            double* re, double* im, double* amp, double* Sk, int64_t* col_sums,
                            int64_t* row_sums) {
   if (!c) return ILG_E_INVALID;
+  NvtxRange nvtx("ilg_observables");
   if (!c->has_state) return fail(c, ILG_E_STATE, "no state: call ilg_init or ilg_set_state first");
   if (nmodes && !modes) return fail(c, ILG_E_INVALID, "modes is NULL");
   bool want_rows = row_sums != nullptr;
@@ -588,8 +606,8 @@ ilg_status ilg_observables(ilg_ctx* c, const int32_t* modes, uint32_t nmodes, ui
     c->d_modes = nullptr;
     c->d_res = nullptr;
     c->mode_cap = 0;
-    ILG_CUDA(c, cudaMalloc(&c->d_modes, sizeof(int32_t) * 2 * nmodes), "cudaMalloc modes");
-    ILG_CUDA(c, cudaMalloc(&c->d_res, sizeof(double) * 4 * nmodes), "cudaMalloc modes");
+    ILG_CUDA(c, dev_alloc(&c->d_modes, sizeof(int32_t) * 2 * nmodes), "cudaMalloc modes");
+    ILG_CUDA(c, dev_alloc(&c->d_res, sizeof(double) * 4 * nmodes), "cudaMalloc modes");
     c->mode_cap = nmodes;
   }
   const uint32_t Lx = c->p.Lx, Ly = c->p.Ly;
@@ -628,8 +646,8 @@ ilg_status ilg_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, size_t 
   if (n == 0) return ILG_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint32_t *d_c = nullptr, *d_o = nullptr;
-  cudaError_t e = cudaMalloc(&d_c, sizeof(uint32_t) * 4 * n);
-  if (e == cudaSuccess) e = cudaMalloc(&d_o, sizeof(uint32_t) * 4 * n);
+  cudaError_t e = dev_alloc(&d_c, sizeof(uint32_t) * 4 * n);
+  if (e == cudaSuccess) e = dev_alloc(&d_o, sizeof(uint32_t) * 4 * n);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_c, ctr, sizeof(uint32_t) * 4 * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_philox(d_c, uint32_t(seed), uint32_t(seed >> 32), d_o, n, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_o, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost, s);

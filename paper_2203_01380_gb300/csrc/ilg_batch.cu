@@ -233,6 +233,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
       src = dst;
       dst = tmp;
       steps_done = s + 1;
+      if (b.states) {
+        // the state after this step, planes rest, +1, -1 as the batch buffer holds them
+        uint16_t* rs = b.states + d.state_off * b.T + size_t(s) * 3 * L;
+        for (uint32_t i = tid; i < 3 * L; i += THREADS) {
+          const uint32_t pl = i >= 2 * L ? 2u : (i >= L ? 1u : 0u);
+          rs[i] = src[pl * b.Lmax + (i - pl * L)];
+        }
+      }
       if (rec) {
         // state s was reduced into slot s & 1 before this step's barrier: finalise
         // it; then the warps reduce the new state s + 1 into the other slot

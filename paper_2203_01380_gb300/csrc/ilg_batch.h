@@ -43,6 +43,8 @@ struct BatchArgs {
                            // after every step; or NULL
   const longlong2* trig;   // fixed-point (cos, sin) of the recorded mode indexed by x when
                            // every ring has one length, else NULL (computed per node)
+  uint16_t* states;        // state of every ring after every step, or NULL: ring r's
+                           // T x 3 L_r occupations at T * state_off, step s at s * 3 L_r
 };
 
 size_t batch_smem_bytes(uint32_t Lmax, int threads);

@@ -38,6 +38,8 @@ struct ilg_batch {
   size_t rec_cap = 0;
   double* d_out = nullptr;            // amplitude record or ensemble statistics
   size_t out_cap = 0;
+  uint16_t* d_states = nullptr;       // per-step states (ilg_batch_run_record), T x total
+  size_t states_cap = 0;
   longlong2* d_trig = nullptr;        // fixed-point trigonometric table of the ensemble mode
   uint32_t trig_cap = 0;
   unsigned long long* d_mass = nullptr;
@@ -47,6 +49,7 @@ struct ilg_batch {
   uint32_t graph_T = 0;
   bool graph_rec = false;
   bool graph_trig = false;
+  bool graph_states = false;
   int32_t graph_mode = 0;
   std::string err;
 };
@@ -89,6 +92,7 @@ void free_batch(ilg_batch* b) {
   cudaFree(b->d_record);
   cudaFree(b->d_rec);
   cudaFree(b->d_out);
+  cudaFree(b->d_states);
   cudaFree(b->d_trig);
   cudaFree(b->d_mass);
   cudaFree(b->d_amp);
@@ -158,14 +162,14 @@ ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, 
   std::iota(order.begin(), order.end(), 0u);
   std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return b->desc[x].L > b->desc[y].L; });
 
-  if ((e = cudaMalloc(&b->d_state, sizeof(uint16_t) * b->total)) != cudaSuccess) return bail(e, "cudaMalloc state");
-  if ((e = cudaMalloc(&b->d_desc, sizeof(ReplicaDesc) * n)) != cudaSuccess) return bail(e, "cudaMalloc desc");
-  if ((e = cudaMalloc(&b->d_tables, sizeof(uint32_t) * tables.size())) != cudaSuccess) return bail(e, "cudaMalloc tables");
-  if ((e = cudaMalloc(&b->d_order, sizeof(uint32_t) * n)) != cudaSuccess) return bail(e, "cudaMalloc order");
-  if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned int))) != cudaSuccess) return bail(e, "cudaMalloc counter");
-  if ((e = cudaMalloc(&b->d_failed, sizeof(uint32_t) * n)) != cudaSuccess) return bail(e, "cudaMalloc flags");
-  if ((e = cudaMalloc(&b->d_mass, sizeof(unsigned long long) * n)) != cudaSuccess) return bail(e, "cudaMalloc mass");
-  if ((e = cudaMalloc(&b->d_amp, sizeof(double) * n)) != cudaSuccess) return bail(e, "cudaMalloc amp");
+  if ((e = dev_alloc(&b->d_state, sizeof(uint16_t) * b->total)) != cudaSuccess) return bail(e, "cudaMalloc state");
+  if ((e = dev_alloc(&b->d_desc, sizeof(ReplicaDesc) * n)) != cudaSuccess) return bail(e, "cudaMalloc desc");
+  if ((e = dev_alloc(&b->d_tables, sizeof(uint32_t) * tables.size())) != cudaSuccess) return bail(e, "cudaMalloc tables");
+  if ((e = dev_alloc(&b->d_order, sizeof(uint32_t) * n)) != cudaSuccess) return bail(e, "cudaMalloc order");
+  if ((e = dev_alloc(&b->d_counter, sizeof(unsigned int))) != cudaSuccess) return bail(e, "cudaMalloc counter");
+  if ((e = dev_alloc(&b->d_failed, sizeof(uint32_t) * n)) != cudaSuccess) return bail(e, "cudaMalloc flags");
+  if ((e = dev_alloc(&b->d_mass, sizeof(unsigned long long) * n)) != cudaSuccess) return bail(e, "cudaMalloc mass");
+  if ((e = dev_alloc(&b->d_amp, sizeof(double) * n)) != cudaSuccess) return bail(e, "cudaMalloc amp");
   if ((e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(ReplicaDesc) * n, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
       (e = cudaMemcpyAsync(b->d_tables, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
       (e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
@@ -204,7 +208,7 @@ ilg_status ilg_batch_init(ilg_batch* b) {
     all.insert(all.end(), its[i].table.begin(), its[i].table.end());
   }
   uint32_t* d_all = nullptr;
-  BCUDA(b, cudaMalloc(&d_all, sizeof(uint32_t) * all.size()), "cudaMalloc init tables");
+  BCUDA(b, dev_alloc(&d_all, sizeof(uint32_t) * all.size()), "cudaMalloc init tables");
   cudaError_t e = cudaMemcpyAsync(d_all, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice, b->stream);
   for (uint32_t i = 0; i < b->n && e == cudaSuccess; ++i) {
     const ilg_params& q = b->p[i];
@@ -268,7 +272,7 @@ namespace {
 // descriptors.  With rec the complex amplitude of record_mode is recorded at the
 // start and after every step (n x (T + 1) x 4 raw 128-bit sums in d_record).
 ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec, bool trig,
-                        std::vector<uint32_t>& failed) {
+                        std::vector<uint32_t>& failed, bool states = false) {
   for (const auto& d : b->desc)
     if (uint64_t(d.t) + T >= (uint64_t(1) << 32)) return bfail(b, ILG_E_INVALID, "step counter would reach 2^32");
   const size_t need = size_t(b->n) * (size_t(T) + 1) * 4;
@@ -276,7 +280,7 @@ ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec,
     cudaFree(b->d_record);
     b->d_record = nullptr;
     b->record_cap = 0;
-    BCUDA(b, cudaMalloc(&b->d_record, sizeof(long long) * need), "cudaMalloc record");
+    BCUDA(b, dev_alloc(&b->d_record, sizeof(long long) * need), "cudaMalloc record");
     b->record_cap = need;
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
@@ -290,7 +294,7 @@ ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec,
       cudaFree(b->d_trig);
       b->d_trig = nullptr;
       b->trig_cap = 0;
-      BCUDA(b, cudaMalloc(&b->d_trig, sizeof(longlong2) * L), "cudaMalloc trig");
+      BCUDA(b, dev_alloc(&b->d_trig, sizeof(longlong2) * L), "cudaMalloc trig");
       b->trig_cap = L;
       if (b->graph) {
         cudaGraphExecDestroy(b->graph);
@@ -299,7 +303,19 @@ ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec,
     }
     BCUDA(b, launch_batch_trig(L, record_mode, b->d_trig, b->stream), "trig table");
   }
-  if (!b->graph || b->graph_T != T || b->graph_rec != rec || b->graph_mode != record_mode || b->graph_trig != trig) {
+  if (states && b->states_cap < size_t(T) * b->total) {
+    cudaFree(b->d_states);
+    b->d_states = nullptr;
+    b->states_cap = 0;
+    BCUDA(b, dev_alloc(&b->d_states, sizeof(uint16_t) * size_t(T) * b->total), "cudaMalloc state record");
+    b->states_cap = size_t(T) * b->total;
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  if (!b->graph || b->graph_T != T || b->graph_rec != rec || b->graph_mode != record_mode || b->graph_trig != trig ||
+      b->graph_states != states) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     BatchArgs a{};
@@ -315,6 +331,7 @@ ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec,
     a.failed = b->d_failed;
     a.record = rec ? b->d_record : nullptr;
     a.trig = trig ? b->d_trig : nullptr;
+    a.states = states ? b->d_states : nullptr;
     cudaGraph_t g = nullptr;
     BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream);
@@ -332,6 +349,7 @@ ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec,
     b->graph_rec = rec;
     b->graph_mode = record_mode;
     b->graph_trig = trig;
+    b->graph_states = states;
   }
   BCUDA(b, cudaGraphLaunch(b->graph, b->stream), "batch launch");
   failed.assign(b->n, 0);
@@ -363,24 +381,27 @@ ilg_status ensure_doubles(ilg_batch* b, double** buf, size_t* cap, size_t need) 
   cudaFree(*buf);
   *buf = nullptr;
   *cap = 0;
-  BCUDA(b, cudaMalloc(buf, sizeof(double) * need), "cudaMalloc");
+  BCUDA(b, dev_alloc(buf, sizeof(double) * need), "cudaMalloc");
   *cap = need;
   return ILG_OK;
 }
 
 }  // namespace
 
-ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record) {
+ilg_status ilg_batch_run_record(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record,
+                                uint16_t* state_record) {
   if (!b) return ILG_E_INVALID;
+  NvtxRange nvtx("ilg_batch_run");
   if (T == 0) return ILG_OK;
   const bool rec = amp_record != nullptr;
+  const bool states = state_record != nullptr;
   std::vector<uint32_t> failed;
   if (rec) {
     ilg_status st = ensure_doubles(b, &b->d_out, &b->out_cap, size_t(b->n) * T);
     if (st == ILG_OK) st = ensure_doubles(b, &b->d_rec, &b->rec_cap, size_t(b->n) * (size_t(T) + 1) * 2);
     if (st != ILG_OK) return st;
   }
-  ilg_status st = batch_launch(b, T, record_mode, rec, false, failed);
+  ilg_status st = batch_launch(b, T, record_mode, rec, false, failed, states);
   if (st != ILG_OK) return st;
   if (rec) {
     BCUDA(b, launch_batch_convert(b->d_desc, b->d_record, b->n, T, b->d_rec, b->stream), "convert record");
@@ -388,11 +409,20 @@ ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* 
     BCUDA(b, cudaMemcpyAsync(amp_record, b->d_out, sizeof(double) * b->n * size_t(T), cudaMemcpyDeviceToHost, b->stream),
           "read record");
   }
+  if (states)
+    BCUDA(b, cudaMemcpyAsync(state_record, b->d_states, sizeof(uint16_t) * size_t(T) * b->total,
+                             cudaMemcpyDeviceToHost, b->stream),
+          "read state record");
   return batch_finish(b, failed);
+}
+
+ilg_status ilg_batch_run(ilg_batch* b, uint32_t T, int32_t record_mode, double* amp_record) {
+  return ilg_batch_run_record(b, T, record_mode, amp_record, nullptr);
 }
 
 ilg_status ilg_batch_ensemble(ilg_batch* b, uint32_t T, int32_t mode, double* stats, double* record) {
   if (!b) return ILG_E_INVALID;
+  NvtxRange nvtx("ilg_batch_ensemble");
   if (!stats) return bfail(b, ILG_E_INVALID, "stats is NULL");
   if (b->n < 2) return bfail(b, ILG_E_INVALID, "an ensemble needs at least two rings");
   for (const auto& d : b->desc)
@@ -436,10 +466,10 @@ ilg_status ilg_batch_autotune(ilg_batch* b, uint32_t trial_steps, ilg_tuning* ou
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   };
-  cudaError_t e = cudaMalloc(&s_state, sizeof(uint16_t) * b->total);
-  if (e == cudaSuccess) e = cudaMalloc(&s_desc, sizeof(ReplicaDesc) * b->n);
-  if (e == cudaSuccess) e = cudaMalloc(&s_counter, sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMalloc(&s_failed, sizeof(uint32_t) * b->n);
+  cudaError_t e = dev_alloc(&s_state, sizeof(uint16_t) * b->total);
+  if (e == cudaSuccess) e = dev_alloc(&s_desc, sizeof(ReplicaDesc) * b->n);
+  if (e == cudaSuccess) e = dev_alloc(&s_counter, sizeof(unsigned int));
+  if (e == cudaSuccess) e = dev_alloc(&s_failed, sizeof(uint32_t) * b->n);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess)

@@ -1,6 +1,9 @@
 // Internal declarations shared by the sources of libilg.so (host side).
 #pragma once
 
+#include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -65,6 +68,24 @@ double initial_mean(const ilg_params& p, int Q, int cls, uint32_t r, uint32_t L)
 uint32_t initial_period(const ilg_params& p);
 
 void set_context_free_error(const std::string& msg);
+
+// NVTX range for the duration of a scope (step, observables, batch run, server
+// round): visible in Nsight timelines, free when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Device allocations of the library go through here: cudaMalloc, unless a failure
+// has been injected (ilg_inject_alloc_failure), in which case the allocation
+// reports cudaErrorMemoryAllocation without calling the allocator.
+cudaError_t dev_malloc(void** p, size_t bytes);
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
 std::string validate_params(const ilg_params& p);   // empty when valid
 void round_keys(uint64_t seed, uint32_t* rk);        // Philox round keys, 20 words
 

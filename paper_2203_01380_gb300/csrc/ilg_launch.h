@@ -36,6 +36,14 @@ cudaError_t launch_step_vec(int Q, const StepArgs& a, const uint16_t* in, uint16
 uint64_t step_seg_units(uint32_t Lx, uint32_t Ly);
 cudaError_t launch_step_seg(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                             unsigned long long* fail, int grid, cudaStream_t s);
+// warp segments of 4-node vectors (ilg_step_warp.cu): rows a multiple of 4, both
+// probabilities drawn through tables; shape 0 = one block of 768 threads per SM,
+// shape 1 = one block of 512 threads; step_warp_grid = blocks of a launch
+cudaError_t prepare_step_warp_kernels();
+uint32_t step_warp_width(int shape);  // nodes per lane (rows must be a multiple)
+uint32_t step_warp_grid(uint32_t Lx, uint32_t Ly, uint32_t sms, int shape);
+cudaError_t launch_step_warp(int Q, int shape, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
+                             unsigned long long* fail, int grid, cudaStream_t s);
 size_t step_tb_smem_bytes(uint32_t B, uint32_t Tb);
 cudaError_t prepare_step_tb_kernel(uint32_t B, uint32_t Tb);
 cudaError_t launch_step_tb(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t0, uint32_t Tb,

@@ -368,15 +368,15 @@ ilg_status ilg_lb_create(const ilg_lb_params* params, void* stream, ilg_lb** out
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t bytes = sizeof(double) * b->Q * b->nodes;
-  if (e == cudaSuccess) e = cudaMalloc(&b->f[0], bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&b->f[1], bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_part, sizeof(double) * b->chunks * p.Lx);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_col, sizeof(double) * p.Lx);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_row, sizeof(double) * b->Ly);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_out, sizeof(double) * (1 + 2 * kLbMaxModes));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_modes, sizeof(int32_t) * 2 * kLbMaxModes);
+  if (e == cudaSuccess) e = ilg::dev_alloc(&b->f[0], bytes);
+  if (e == cudaSuccess) e = ilg::dev_alloc(&b->f[1], bytes);
+  if (e == cudaSuccess) e = ilg::dev_alloc(&b->d_part, sizeof(double) * b->chunks * p.Lx);
+  if (e == cudaSuccess) e = ilg::dev_alloc(&b->d_col, sizeof(double) * p.Lx);
+  if (e == cudaSuccess) e = ilg::dev_alloc(&b->d_row, sizeof(double) * b->Ly);
+  if (e == cudaSuccess) e = ilg::dev_alloc(&b->d_out, sizeof(double) * (1 + 2 * kLbMaxModes));
+  if (e == cudaSuccess) e = ilg::dev_alloc(&b->d_modes, sizeof(int32_t) * 2 * kLbMaxModes);
   const size_t maxL = p.Lx > b->Ly ? p.Lx : b->Ly;
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_red, sizeof(double2) * 2 * kLbMaxModes * ((maxL + kLbChunk - 1) / kLbChunk));
+  if (e == cudaSuccess) e = ilg::dev_alloc(&b->d_red, sizeof(double2) * 2 * kLbMaxModes * ((maxL + kLbChunk - 1) / kLbChunk));
   if (e != cudaSuccess) {
     ilg_lb_destroy(b);
     return lb_cuda_fail(nullptr, e, "ilg_lb_create");
@@ -402,6 +402,20 @@ ilg_status ilg_lb_destroy(ilg_lb* b) {
 
 const char* ilg_lb_last_error(const ilg_lb* b) { return b ? b->err.c_str() : ilg_last_error(nullptr); }
 
+// Sec. IV, Eq. omegaj: with the flip (omega_eff > 1) the collision fraction is
+// omega* = 2 - omega_eff; the current then relaxes with omega^j = 2 - omega* and the
+// even moments with omega*.  Without the flip every non-conserved moment relaxes with
+// omega_eff.
+ilg_status ilg_lb_rates(double omega_eff, double* omega_j, double* omega) {
+  if (!omega_j || !omega || !(omega_eff > 0.0 && omega_eff <= 2.0)) {
+    ilg::set_context_free_error("ilg_lb_rates: omega_eff must lie in (0, 2] and the outputs be non-NULL");
+    return ILG_E_INVALID;
+  }
+  *omega_j = omega_eff;
+  *omega = omega_eff > 1.0 ? 2.0 - omega_eff : omega_eff;
+  return ILG_OK;
+}
+
 ilg_status ilg_lb_init(ilg_lb* b) {
   if (!b) return ILG_E_INVALID;
   const ilg_params g = as_gas(b->p);
@@ -424,7 +438,7 @@ ilg_status ilg_lb_init(ilg_lb* b) {
     mode = uint32_t(((m % L) + L) % L);
   }
   double* d_lam = nullptr;
-  LB_CUDA(b, cudaMalloc(&d_lam, sizeof(double) * lam.size()), "cudaMalloc");
+  LB_CUDA(b, ilg::dev_alloc(&d_lam, sizeof(double) * lam.size()), "cudaMalloc");
   cudaError_t e = cudaMemcpyAsync(d_lam, lam.data(), sizeof(double) * lam.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) {
     if (b->Q == 3)

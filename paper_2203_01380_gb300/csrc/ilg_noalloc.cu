@@ -1,13 +1,15 @@
 // Observables of a caller-held device state without any device allocation.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// observables: code that runs while a stream is being captured into a CUDA graph
-// (cudaMalloc is not allowed there), real-time loops that must not take the
-// allocator's locks or implicit synchronisation, and hosts whose device memory
-// all belongs to their own pool.  ilg_observables_noalloc serves them: it runs
-// the same reduction and projection kernels as ilg_observables, but its scratch
-// (column and row sums, mass, modes, results) is the file-scope array below,
-// which every GPU that loads the library holds until the process exits.
+// observables: applications whose device memory already belongs to their own
+// pool (a framework's caching allocator that holds the free HBM, so cudaMalloc
+// would fail), and real-time loops that must not wait on the allocator's locks or
+// on the device-wide synchronisation that freeing memory implies.
+// ilg_observables_noalloc serves them: it runs the same reduction and projection
+// kernels as ilg_observables, but its scratch (column and row sums, mass, modes,
+// results) is the file-scope array below, which every GPU that loads the library
+// holds until the process exits.  The call still synchronises its stream to
+// return the results.
 #include <cuda_runtime.h>
 
 #include <mutex>

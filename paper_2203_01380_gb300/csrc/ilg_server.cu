@@ -124,6 +124,17 @@ struct ilg_server {
   double* d_res = nullptr;
   StepArgs common{};
   std::chrono::steady_clock::time_point t0;
+  // admissions: a newcomer's tables and Poisson initial state are written on their own
+  // stream; the serving stream waits on the event before the next round, and the
+  // arena memory of its initial-state tables returns once the event has completed
+  cudaStream_t init_stream = nullptr;
+  struct PendingInit {
+    cudaEvent_t ev;
+    size_t off, bytes;
+  };
+  std::vector<PendingInit> inits;
+  cudaEvent_t round_ev = nullptr;   // end of a round's launches and its flag read-back
+  uint32_t* h_fail = nullptr;       // pinned: per-lattice overflow flags of a round
 
   std::thread worker;
   std::mutex mu;
@@ -144,6 +155,11 @@ namespace {
 thread_local std::string g_server_create_error;
 
 void free_server(ilg_server* s) {
+  for (auto& pi : s->inits) cudaEventDestroy(pi.ev);
+  s->inits.clear();
+  if (s->round_ev) cudaEventDestroy(s->round_ev);
+  if (s->h_fail) cudaFreeHost(s->h_fail);
+  if (s->init_stream) cudaStreamDestroy(s->init_stream);
   cudaFree(s->d_arena);
   cudaFree(s->d_lat);
   cudaFree(s->d_items);
@@ -201,9 +217,11 @@ bool admit(ilg_server* s, const Request& rq, Resident* out, cudaError_t* cerr, s
   std::copy(it.count.begin(), it.count.end(), init.begin() + it.offset.size());
   std::copy(it.table.begin(), it.table.end(), init.begin() + it.offset.size() + it.count.size());
   uint32_t* d_init = reinterpret_cast<uint32_t*>(s->d_arena + off_init);
-  cudaError_t e = cudaMemcpyAsync(s->d_arena + r.off_tab, tables.data(), tab_bytes, cudaMemcpyHostToDevice, s->stream);
+  // (copies from pageable host memory: the source is consumed before the call returns)
+  cudaError_t e =
+      cudaMemcpyAsync(s->d_arena + r.off_tab, tables.data(), tab_bytes, cudaMemcpyHostToDevice, s->init_stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_init, init.data(), sizeof(uint32_t) * init_words, cudaMemcpyHostToDevice, s->stream);
+    e = cudaMemcpyAsync(d_init, init.data(), sizeof(uint32_t) * init_words, cudaMemcpyHostToDevice, s->init_stream);
   if (e == cudaSuccess) {
     InitArgs a{};
     a.Lx = rq.p.Lx;
@@ -222,16 +240,22 @@ bool admit(ilg_server* s, const Request& rq, Resident* out, cudaError_t* cerr, s
     a.table = d_init + it.offset.size() + it.count.size();
     const size_t nodes = size_t(rq.p.Lx) * rq.p.Ly;
     const int grid = int(std::min<size_t>((nodes + 255) / 256, size_t(s->sms) * 4));
-    e = launch_init(5, a, reinterpret_cast<uint16_t*>(s->d_arena + r.off_state), grid, s->stream);
+    e = launch_init(5, a, reinterpret_cast<uint16_t*>(s->d_arena + r.off_state), grid, s->init_stream);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  s->arena.release(off_init, sizeof(uint32_t) * init_words);
+  cudaEvent_t ev = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, s->init_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, ev, 0);
   if (e != cudaSuccess) {
     *cerr = e;
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamSynchronize(s->init_stream);
+    s->arena.release(off_init, sizeof(uint32_t) * init_words);
     s->arena.release(r.off_state, 2 * r.state_bytes);
     s->arena.release(r.off_tab, tab_bytes);
     return false;
   }
+  s->inits.push_back(ilg_server::PendingInit{ev, off_init, sizeof(uint32_t) * init_words});
   r.t = 0;
   r.remaining = rq.steps;
   r.phase = 0;
@@ -274,12 +298,68 @@ cudaError_t finish(ilg_server* s, Resident& r, ilg_result* res) {
   return e;
 }
 
+// Initial states whose event has completed give their tables' arena memory back.
+cudaError_t release_inits(ilg_server* s) {
+  size_t k = 0;
+  for (size_t i = 0; i < s->inits.size(); ++i) {
+    const cudaError_t q = cudaEventQuery(s->inits[i].ev);
+    if (q == cudaSuccess) {
+      cudaEventDestroy(s->inits[i].ev);
+      s->arena.release(s->inits[i].off, s->inits[i].bytes);
+    } else if (q == cudaErrorNotReady) {
+      s->inits[k++] = s->inits[i];
+    } else {
+      return q;
+    }
+  }
+  s->inits.resize(k);
+  return cudaSuccess;
+}
+
+// Admission: in arrival order (or least work first) while slots and arena memory
+// allow; every admitted request's initial state is queued on the admission stream.
+void admit_pending(ilg_server* s, cudaError_t& e) {
+  e = release_inits(s);
+  if (e != cudaSuccess) return;
+  for (;;) {
+    Request rq;
+    size_t pick = 0;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->pending.empty() || s->resident.size() >= s->max_slots) break;
+      if (s->policy == ILG_ADMIT_SMALLEST) {
+        // least work (node updates) first
+        double best = -1.0;
+        for (size_t k = 0; k < s->pending.size(); ++k) {
+          const Request& q = s->pending[k];
+          const double w = double(q.p.Lx) * q.p.Ly * q.steps;
+          if (best < 0.0 || w < best) {
+            best = w;
+            pick = k;
+          }
+        }
+      }
+      rq = s->pending[pick];
+    }
+    Resident r;
+    std::string msg;
+    if (!admit(s, rq, &r, &e, &msg)) {
+      if (e != cudaSuccess) break;
+      break;  // wait for memory to come back
+    }
+    r.t_admit = now_s(s->t0);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->pending.erase(s->pending.begin() + long(pick));
+    s->resident.push_back(r);
+    s->peak_resident = std::max<uint32_t>(s->peak_resident, uint32_t(s->resident.size()));
+  }
+}
+
 void worker_main(ilg_server* s) {
   cudaError_t e = cudaSuccess;
   std::vector<LatDesc> lat;
   std::vector<WorkItem> items;
   for (;;) {
-    std::vector<Request> admit_now;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv.wait(lk, [&] { return s->stop || !s->pending.empty() || !s->resident.empty(); });
@@ -291,39 +371,8 @@ void worker_main(ilg_server* s) {
       }
     }
     const double t_round = now_s(s->t0);
-    // admission: in arrival order while slots and arena memory allow
-    for (;;) {
-      Request rq;
-      size_t pick = 0;
-      {
-        std::lock_guard<std::mutex> lk(s->mu);
-        if (s->pending.empty() || s->resident.size() >= s->max_slots) break;
-        if (s->policy == ILG_ADMIT_SMALLEST) {
-          // least work (node updates) first
-          double best = -1.0;
-          for (size_t k = 0; k < s->pending.size(); ++k) {
-            const Request& q = s->pending[k];
-            const double w = double(q.p.Lx) * q.p.Ly * q.steps;
-            if (best < 0.0 || w < best) {
-              best = w;
-              pick = k;
-            }
-          }
-        }
-        rq = s->pending[pick];
-      }
-      Resident r;
-      std::string msg;
-      if (!admit(s, rq, &r, &e, &msg)) {
-        if (e != cudaSuccess) break;
-        break;  // wait for memory to come back
-      }
-      r.t_admit = now_s(s->t0);
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->pending.erase(s->pending.begin() + long(pick));
-      s->resident.push_back(r);
-      s->peak_resident = std::max<uint32_t>(s->peak_resident, uint32_t(s->resident.size()));
-    }
+    NvtxRange nvtx("ilg_server round");
+    admit_pending(s, e);
     double round_updates = 0;
     if (e != cudaSuccess) break;
     // one round: up to `quantum` steps, each lattice taking min(quantum, remaining)
@@ -361,7 +410,7 @@ void worker_main(ilg_server* s) {
       if (items.size() > s->items_cap) {
         cudaFree(s->d_items);
         s->d_items = nullptr;
-        e = cudaMalloc(&s->d_items, sizeof(WorkItem) * items.size() * 2);
+        e = dev_alloc(&s->d_items, sizeof(WorkItem) * items.size() * 2);
         if (e != cudaSuccess) break;
         s->items_cap = items.size() * 2;
       }
@@ -379,11 +428,23 @@ void worker_main(ilg_server* s) {
       // persistent blocks: as many as are resident at once (3 per SM at this register count)
       const int grid = int(std::min<size_t>(items.size(), size_t(s->sms) * kMultiBlocksPerSm));
       for (uint32_t sub = 0; sub < q && e == cudaSuccess; ++sub) e = launch_multi_step(ma, s->common, sub, grid, s->stream);
-      std::vector<uint32_t> fail(lat.size());
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(fail.data(), s->d_fail, sizeof(uint32_t) * lat.size(), cudaMemcpyDeviceToHost, s->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        e = cudaMemcpyAsync(s->h_fail, s->d_fail, sizeof(uint32_t) * lat.size(), cudaMemcpyDeviceToHost, s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(s->round_ev, s->stream);
+      // while the round runs, requests that arrive are admitted (their initial states
+      // queued on the admission stream, for the next round)
+      while (e == cudaSuccess) {
+        const cudaError_t q_ = cudaEventQuery(s->round_ev);
+        if (q_ == cudaSuccess) break;
+        if (q_ != cudaErrorNotReady) {
+          e = q_;
+          break;
+        }
+        admit_pending(s, e);
+        if (e == cudaSuccess) std::this_thread::sleep_for(std::chrono::microseconds(50));
+      }
       if (e != cudaSuccess) break;
+      const uint32_t* fail = s->h_fail;
       for (size_t j = 0; j < which.size(); ++j) {
         Resident& r = s->resident[which[j]];
         const uint32_t done = fail[j] == 0xFFFFFFFFu ? lat[j].steps : fail[j];
@@ -461,20 +522,25 @@ ilg_status ilg_server_create(uint64_t seed, uint64_t hbm_bytes, uint32_t max_slo
     if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "cudaStreamCreate");
     s->own_stream = true;
   }
-  if ((e = cudaMalloc(&s->d_arena, hbm_bytes)) != cudaSuccess) return bail(e, "cudaMalloc arena");
+  if ((e = dev_alloc(&s->d_arena, hbm_bytes)) != cudaSuccess) return bail(e, "cudaMalloc arena");
   s->arena_bytes = hbm_bytes;
   s->arena.reset(hbm_bytes);
-  if ((e = cudaMalloc(&s->d_lat, sizeof(LatDesc) * max_slots)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&s->d_counters, sizeof(unsigned int) * quantum)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&s->d_fail, sizeof(uint32_t) * max_slots)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&s->d_col, sizeof(unsigned long long) * kServerMaxSide)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&s->d_row, sizeof(unsigned long long) * kServerMaxSide)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&s->d_mass, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&s->d_modes, sizeof(int32_t) * 2)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&s->d_res, sizeof(double) * 4)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dev_alloc(&s->d_lat, sizeof(LatDesc) * max_slots)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dev_alloc(&s->d_counters, sizeof(unsigned int) * quantum)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dev_alloc(&s->d_fail, sizeof(uint32_t) * max_slots)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dev_alloc(&s->d_col, sizeof(unsigned long long) * kServerMaxSide)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dev_alloc(&s->d_row, sizeof(unsigned long long) * kServerMaxSide)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dev_alloc(&s->d_mass, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dev_alloc(&s->d_modes, sizeof(int32_t) * 2)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dev_alloc(&s->d_res, sizeof(double) * 4)) != cudaSuccess) return bail(e, "cudaMalloc");
   const int32_t mode1[2] = {1, 0};
   if ((e = cudaMemcpy(s->d_modes, mode1, sizeof(mode1), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "upload");
   if ((e = prepare_multi_kernel()) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
+  if ((e = cudaStreamCreateWithFlags(&s->init_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(e, "cudaStreamCreate");
+  if ((e = cudaEventCreateWithFlags(&s->round_ev, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e, "cudaEventCreate");
+  if ((e = cudaMallocHost(&s->h_fail, sizeof(uint32_t) * max_slots)) != cudaSuccess) return bail(e, "cudaMallocHost");
   round_keys(seed, s->common.rk);
   s->common.key0 = uint32_t(seed);
   s->common.key1 = uint32_t(seed >> 32);
@@ -570,6 +636,7 @@ ilg_status ilg_server_destroy(ilg_server* s) {
   }
   if (s->worker.joinable()) s->worker.join();
   cudaStreamSynchronize(s->stream);
+  if (s->init_stream) cudaStreamSynchronize(s->init_stream);
   free_server(s);
   delete s;
   return ILG_OK;

@@ -4,6 +4,8 @@
 // defined by a fixed sequence of IEEE double operations and libm calls, and must
 // come out the same on every host.
 #include <algorithm>
+#include <atomic>
+
 #include "ilg_internal.h"
 
 #include <cmath>
@@ -247,4 +249,30 @@ bool build_init_tables(const ilg_params& p, int Q, InitTables* out, std::string*
   return true;
 }
 
+namespace {
+// allocations still to succeed before the injected failure; negative: none injected
+std::atomic<int64_t> g_alloc_countdown{-1};
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int64_t left = g_alloc_countdown.load();
+  while (left >= 0) {
+    // take one allocation off the countdown; the one that finds it at 0 fails
+    if (g_alloc_countdown.compare_exchange_weak(left, left - 1)) {
+      if (left == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 }  // namespace ilg
+
+extern "C" ilg_status ilg_inject_alloc_failure(int64_t after) {
+  ilg::g_alloc_countdown.store(after < 0 ? -1 : after);
+  return ILG_OK;
+}
+

@@ -16,7 +16,7 @@ def B():
     return binding
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 5, -1])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 5, 6, 7, -1])
 @pytest.mark.parametrize("lattice,Lx,Ly,mean,hot", [(2, 96, 40, 10.0, 3), (2, 100, 23, 8.0, 0), (1, 2052, 1, 20.0, 2),
                                                     (2, 2056, 9, 6.0, 0), (2, 8200, 3, 6.0, 1),
                                                     (1, 16392, 1, 20.0, 2)])
@@ -24,7 +24,8 @@ def test_every_shape_is_bit_exact(B, kernel, lattice, Lx, Ly, mean, hot):
     """8- and 4-node vectors in row tiles, 8-node vectors in warp segments (rows of 96,
     100, 2052, 2056 nodes: several tiles, ragged tails, occupations that need the
     general pass; rows of 8200 and 16392 nodes: segments of 8192 nodes and a one-vector
-    remainder), node-parallel, default."""
+    remainder), 4-node vectors in warp segments (the row split into segments whose
+    end values are stored by the warp that owns them), node-parallel, default."""
     Q = 3 if lattice == 1 else 5
     s0 = inputs.random_state(Q, Ly, Lx, mean, seed=Lx + Ly, hot=hot, hot_value=500)
     cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, omega_eff=1.7, seed=9, replica=1)
@@ -46,7 +47,7 @@ def test_autotune_keeps_state_and_results(B):
         tun = lat.autotune(6)
         after, t1 = lat.get_state()
         assert t0 == t1 == 3 and np.array_equal(before, after)
-        assert set(tun["ms_per_step"]) == {"vec8", "vec4", "node", "tb2", "tb4", "seg8"}
+        assert set(tun["ms_per_step"]) == {"vec8", "vec4", "node", "tb2", "tb4", "seg8", "warp768", "warp512"}
         assert all(v is not None and v > 0 for v in tun["ms_per_step"].values())
         assert tun["ms_per_step"][tun["choice"]] == min(tun["ms_per_step"].values())
         lat.step(9)
@@ -56,13 +57,15 @@ def test_autotune_keeps_state_and_results(B):
 
 @pytest.mark.parametrize("cfg,applicable", [
     (dict(lattice=1, Lx=1028, n0=10.0), {"vec8": False, "vec4": True, "node": True, "tb2": False, "tb4": False,
-                                         "seg8": False}),
+                                         "seg8": False, "warp768": True, "warp512": True}),
     (dict(lattice=3, Lx=64, Ly=32, n0=10.0), {"vec8": False, "vec4": False, "node": True, "tb2": False, "tb4": False,
-                                              "seg8": False}),
+                                              "seg8": False, "warp768": False, "warp512": False}),
     (dict(lattice=2, Lx=64, Ly=32, n0=80.0), {"vec8": False, "vec4": False, "node": True, "tb2": True, "tb4": True,
-                                              "seg8": False}),
+                                              "seg8": False, "warp768": False, "warp512": False}),
     (dict(lattice=2, Lx=1024, Ly=24, n0=10.0), {"vec8": True, "vec4": True, "node": True, "tb2": True, "tb4": True,
-                                               "seg8": True}),
+                                               "seg8": True, "warp768": True, "warp512": True}),
+    (dict(lattice=2, Lx=1020, Ly=6, n0=10.0), {"vec8": False, "vec4": True, "node": True, "tb2": True, "tb4": True,
+                                              "seg8": False, "warp768": True, "warp512": True}),
 ])
 def test_autotune_candidates(B, cfg, applicable):
     with B.Lattice(omega_eff=1.5, seed=2, **cfg) as lat:

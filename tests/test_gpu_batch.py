@@ -170,3 +170,29 @@ def test_batch_workload_full_size(B):
     win = ref.window(x0, 0, w, 1, T)      # light cone wider than the ring: wraps around it
     xs = [(x0 + k) % L for k in range(w)]
     assert np.array_equal(got[:, :, xs], win)
+
+
+def test_run_record_states_and_amplitudes_every_step(B):
+    """ilg_batch_run_record: the state of every ring after every step equals the
+    oracle's step by step, and the amplitude record equals ilg_batch_run's; rings of
+    three lengths (the ring workload's L = 256, an odd length, one above a block)."""
+    reps = [dict(inputs.RING_D1Q3, replica=0),
+            dict(lattice=1, Lx=37, n0=12.0, amp=3.0, mode_mx=1, omega_eff=0.7, seed=1, replica=1),
+            dict(lattice=1, Lx=1100, n0=8.0, amp=2.0, mode_mx=2, omega_eff=1.9, seed=1, replica=2)]
+    reps = [{k: v for k, v in r.items() if k != "steps"} for r in reps]
+    T = 25
+    with B.Batch(reps) as bat:
+        bat.init()
+        amp, states = bat.run_record(T, record_mode=1)
+        got_end = [bat.get_state(i)[0] for i in range(len(reps))]
+    with B.Batch(reps) as bat:
+        bat.init()
+        amp_plain = bat.run(T, record_mode=1)
+    assert np.array_equal(amp, amp_plain)
+    for i, r in enumerate(reps):
+        ref = O.Lattice(**r)
+        s = ref.init()
+        for step in range(T):
+            s = ref.step(s, step)
+            assert np.array_equal(states[i][step], s), (i, step)
+        assert np.array_equal(states[i][T - 1], got_end[i])

@@ -44,3 +44,16 @@ def test_table_arguments_are_checked(B):
         B.poisson_table(700.5)
     with pytest.raises(B.IlgError):
         B.poisson_table(-1.0)
+
+
+@pytest.mark.parametrize("omega_eff", [0.2, 0.5, 1.0, 1.0000001, 1.5, 1.8, 2.0])
+def test_lb_rates_match_the_oracle(B, omega_eff):
+    """ilg_lb_rates (host only) against the oracle's mapping of Sec. IV, Eq. omegaj."""
+    from oracle import lb as L
+    assert B.lb_rates(omega_eff) == tuple(L.rates_from_omega_eff(omega_eff))
+
+
+@pytest.mark.parametrize("omega_eff", [0.0, -1.0, 2.5, float("nan")])
+def test_lb_rates_refuse_bad_parameters(B, omega_eff):
+    with pytest.raises(B.IlgError):
+        B.lb_rates(omega_eff)

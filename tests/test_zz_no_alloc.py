@@ -1,6 +1,7 @@
 """ilg_observables_noalloc, the entry point for callers that cannot allocate
-device memory when they need the observables (inside a stream capture, in
-real-time loops, under a host-owned memory pool): it must give the same mass,
+device memory when they need the observables (applications whose device memory
+belongs to their own pool, real-time loops that must not wait on the allocator):
+it must give the same mass,
 projections, amplitudes and structure factors as ilg_observables on the same
 state, call after call, although its scratch is one static device array shared
 by every call.  This file is collected last so that a failure here never hides
@@ -29,11 +30,19 @@ def _device_copy(torch, B, lat):
     return buf
 
 
-@pytest.mark.parametrize("lattice,Lx,Ly", [(2, 96, 40), (1, 256, 1), (2, 37, 53)])
-def test_noalloc_matches_observables_twice(B, lattice, Lx, Ly):
+MODES_2D = [(1, 0), (2, 0), (-3, 0), (0, 1), (0, 4)]
+
+
+@pytest.mark.parametrize("lattice,Lx,Ly,modes", [
+    (2, 96, 40, MODES_2D), (1, 256, 1, [(1, 0), (2, 0), (-3, 0)]), (2, 37, 53, MODES_2D),
+    (3, 48, 20, MODES_2D),                                   # D2Q9: nine planes
+    (2, 40, 24, []),                                         # mass only (no projection)
+    (2, 32768, 3, [(m, 0) for m in range(1, 257)]),          # the side and mode limits
+    (2, 3, 32768, [(0, 1), (0, 16384), (0, 32767)]),
+])
+def test_noalloc_matches_observables_twice(B, lattice, Lx, Ly, modes):
     torch = pytest.importorskip("torch")
-    Q = 3 if lattice == 1 else 5
-    modes = [(1, 0), (2, 0), (-3, 0)] + ([(0, 1), (0, 4)] if lattice == 2 else [])
+    Q = {1: 3, 2: 5, 3: 9}[lattice]
     cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, omega_eff=1.7, seed=11)
     with B.Lattice(**cfg) as lat:
         for call, seed in enumerate((21, 22)):
