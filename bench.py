@@ -34,17 +34,22 @@ from paper_2203_01380_gb300 import inputs  # noqa: E402
 
 METRIC = "GNUPS (node-updates/s) D2Q5 ILG+flip vs HBM roofline; batched vs plain; p99"
 BYTES_PER_NU = 20  # read + write of 5 uint16 occupations
-# integer operations of the method per D2Q5 node update (two Philox4x32-10 blocks of
-# 80 int32 operations, six alias draws of 4, the redistribution split and the
-# occupation bookkeeping); the peak is one int32 lane-operation per cycle on each of
-# the 32 integer lanes (ALU + FMA-heavy pipes) of the 4 sub-partitions of 152 SMs
-OPS_PER_NU = 209
-INT_LANES_PER_SM_CYCLE = 128
+# random numbers of the method per D2Q5 node update: eight 32-bit words (thinning of
+# the five velocities, the rest share, the axis and sign words of the moving
+# particles), i.e. two Philox4x32-10 blocks
+PHILOX_BLOCKS_PER_NU = 2
 SMS = 152
-# DRAM bytes (read + write) of one 16384^2 launch of a step kernel, from the ncu
-# capture summarised in profiles/ (scaled from a 4096^2 launch by node count); only
+# DRAM bytes (read + write) of one 16384^2 launch of a step kernel, from an ncu
+# capture of the same kernel (scaled from a smaller lattice by node count); only
 # kernels unchanged since their capture are listed
 TRAFFIC_BYTES_PER_LAUNCH = {"seg8": 5.187e9}
+
+
+def json_default(o):
+    """numpy scalars and arrays in the line as plain JSON values."""
+    if hasattr(o, "tolist"):
+        return o.tolist()
+    raise TypeError(f"{type(o).__name__} is not JSON serialisable")
 
 
 def peaks():
@@ -178,33 +183,57 @@ def oracle_all_cores(cfg, side, steps, seconds):
 
 
 KERNEL_NAMES = {"vec8": "step_vec_kernel<5, 8>", "vec4": "step_vec_kernel<5, 4>", "node": "step_kernel<5>",
-                "tb2": "step_tb_kernel (depth 2)", "tb4": "step_tb_kernel (depth 4)", "seg8": "step_seg_kernel<5, 8>"}
+                "tb2": "step_tb_kernel (depth 2)", "tb4": "step_tb_kernel (depth 4)", "seg8": "step_seg_kernel<5, 8>",
+                "warpv8": "step_warp_kernel<5, flip, 64 rows, 8 nodes per lane, 384 threads>",
+                "warpv4": "step_warp_kernel<5, flip, 64 rows, 4 nodes per lane, 768 threads>"}
 
 
-def alu_roofline(nodes, launch_ms, clocks, choice="seg8"):
-    """The step kernel is bound by integer issue: OPS_PER_NU algorithmic int32
-    operations per node update against 128 int32 lane-operations per SM per cycle
-    at the SM clock measured during the run."""
-    mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    peak = INT_LANES_PER_SM_CYCLE * SMS * mhz * 1e6 / 1e9          # Gop/s
-    achieved = OPS_PER_NU * nodes / (launch_ms / 1e3) / 1e9
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(choice),
-            "kernel": KERNEL_NAMES.get(choice, choice), "launch_ms": launch_ms,
-            "ops_per_node_update": OPS_PER_NU, "peak_clock_mhz": mhz}
+def hbm_roofline(nodes, launch_ms, choice):
+    """Sec. 8(d)'s roofline of the dominant kernel: every occupation read and written
+    once (20 B per D2Q5 node update) per launch, against the measured copy bandwidth."""
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    achieved = nodes * BYTES_PER_NU / (launch_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(choice), "kernel": KERNEL_NAMES.get(choice, choice),
+            "launch_ms": launch_ms, "algorithmic_bytes_per_launch": nodes * BYTES_PER_NU,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else "fallback 6800 GB/s (of fallback)"}
 
 
-def measure_batched(torch, B, dev, rings=4096, T=5000):
+def alu_roofline(B, nodes, launch_ms, stream):
+    """The integer bound beside it: the method's random numbers (two Philox4x32-10
+    blocks per node update) against the Philox block rate of this GPU, measured here
+    by ilg_int_peak (1 s of CUDA-event-timed blocks on every SM); and the rate of an
+    even mix of 3-input logic and multiply-add lane-operations for context."""
+    ph = B.int_peak(0, 1.0, stream)
+    mix = B.int_peak(4, 1.0, stream)
+    achieved = PHILOX_BLOCKS_PER_NU * nodes / (launch_ms / 1e3)
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": ph["rate"] / 1e9,
+            "unit": "G Philox4x32-10 blocks/s", "frac": achieved / ph["rate"],
+            "blocks_per_node_update": PHILOX_BLOCKS_PER_NU,
+            "peak_source": "ilg_int_peak kind 0, measured in this run (of measured)",
+            "int_lane_ops_peak": {"value": mix["rate"] / 1e12, "unit": "T int32 lane-ops/s",
+                                  "kind": "even mix of lop3 and 32-bit multiply-add (ilg_int_peak kind 4)"}}
+
+
+def measure_batched(torch, B, dev, rings=4096, T=5000, sample=64):
     """4096 D1Q3 rings, 5000 steps in one persistent launch, against one context per
-    ring on a sample of 16 rings (500 steps each) at identical results.  Fewer rings or
-    steps only for profiling captures."""
+    ring on a stratified sample of the rings (every rings/sample-th ring in order of
+    length), each created and initialised before its timing and timed over the same
+    5000 steps with CUDA events on its stream; the sampled rings' final states must be
+    identical in both runs.  The plain time of all rings is the sample's time scaled by
+    rings/sample (each sampled ring stands for that many rings of similar length).
+    Fewer rings or steps only for profiling captures."""
     reps = inputs.batch_replicas(rings)
     nodes = sum(r["Lx"] for r in reps)
     st = torch.cuda.Stream(dev)
+    by_len = sorted(range(len(reps)), key=lambda i: reps[i]["Lx"])
+    idx = [by_len[k] for k in np.linspace(0, len(reps) - 1, min(sample, len(reps))).astype(int)]
     with B.Batch(reps, stream=st) as bat:
         bat.init()
         tuning = bat.autotune(50)
         bat.run(20)
+        bat.init()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         e0.record(st)
@@ -212,22 +241,36 @@ def measure_batched(torch, B, dev, rings=4096, T=5000):
         e1.record(st)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1)
-    idx = np.linspace(0, len(reps) - 1, 16).astype(int)
-    pn, t0 = 0, time.perf_counter()
+        batch_states = {i: bat.get_state(i)[0] for i in idx}
+    # one context per sampled ring, created and initialised outside the timed region
+    with B.Lattice(**reps[idx[-1]], stream=st) as warm:
+        warm.init()
+        warm.step(50)
+    plain_ms, plain_nu, same = 0.0, 0, True
     for i in idx:
         with B.Lattice(**reps[i], stream=st) as lat:
             lat.init()
-            lat.step(500)
-        pn += reps[i]["Lx"] * 500
-    plain_s = time.perf_counter() - t0
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(st)
+            lat.step(T)
+            b.record(st)
+            torch.cuda.synchronize(dev)
+            plain_ms += a.elapsed_time(b)
+            plain_nu += reps[i]["Lx"] * T
+            same &= bool(np.array_equal(lat.get_state()[0], batch_states[i]))
     v = nodes * T / (ms / 1e3) / 1e9
-    vp = pn / plain_s / 1e9
+    plain_all_ms = plain_ms * len(reps) / len(idx)
     return {"workload": f"batch_d1q3: {rings} rings, L log-uniform [64, 8192], n0 uniform [5, 200], "
                         f"omega_eff uniform [0.2, 1.95], {T} steps, one persistent graph-captured launch",
             "value": v, "unit": "GNUPS", "ms": ms, "node_updates": nodes * T,
-            "plain_per_ring_launch": {"value": vp, "unit": "GNUPS",
-                                      "sample": "16 rings (evenly spaced in the list), init + 500 steps each, one context each, host wall clock"},
-            "speedup_vs_plain": v / vp, "autotune": tuning}
+            "plain_per_ring_launch": {
+                "value": plain_nu / (plain_ms / 1e3) / 1e9, "unit": "GNUPS", "ms_sample": plain_ms,
+                "ms_all_rings_estimated": plain_all_ms,
+                "sample": f"{len(idx)} rings evenly spaced in order of length, one context each, created and "
+                          f"initialised before timing, {T} steps each (one launch per step) timed with CUDA events",
+                "identical_results": same},
+            "speedup_vs_plain": plain_all_ms / ms, "autotune": tuning}
 
 
 FP64_LANES_PER_SM_CYCLE = 2.0   # GB300 nominal 1.25 TFLOP/s fp64 = 2 fused multiply-add lanes per SM per cycle at 2070 MHz
@@ -327,29 +370,92 @@ def measure_particle(torch, B, dev, side):
 
 
 def measure_sweep(torch, B, dev):
-    """The omega sweep workload (D2Q5 1024^2, mean 50 per velocity + a sine of amplitude
-    20), each omega_eff autotuned and timed over 200 steps: at these occupations most
-    nodes need the general collision (chunked binomials, extension words)."""
+    """The omega sweep workload as stated: D2Q5 1024^2, mean 50 per velocity + a sine of
+    amplitude 20 along x, 1000 steps per omega_eff, each autotuned.  The steps are timed
+    with CUDA events; A^LG of mode 1 is read every 10 steps (outside the timed steps) and
+    ln A(t) fitted over t in [100, 1000] for the diffusion constant, against
+    D = theta (1/omega^j - 1/2) (Sec. IV) and against the lattice Boltzmann comparator's
+    mean amplitude from the same initial means (the exact ensemble mean, Sec. IV)."""
     out = {}
     st = torch.cuda.Stream(dev)
-    T = 200
+    every = 10
     for c in inputs.SWEEP_D2Q5:
+        T = c["steps"]
         cfg = {k: v for k, v in c.items() if k != "steps"}
+        k2 = (2.0 * math.pi / cfg["Lx"]) ** 2
         with B.Lattice(**cfg, stream=st) as lat:
             lat.init()
             tun = lat.autotune(10)
-            lat.step(10)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize(dev)
-            e0.record(st)
-            lat.step(T)
-            e1.record(st)
-            torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1) / T
-        out[str(c["omega_eff"])] = {"value": cfg["Lx"] * cfg["Ly"] / (ms / 1e3) / 1e9, "unit": "GNUPS",
-                                    "ms_per_step": ms, "kernel": tun["choice"]}
-    return {"workload": f"sweep_d2q5: D2Q5 1024x1024, Poisson mean 50 per velocity + sine amplitude 20, "
-                        f"{T} steps per omega_eff", "omega_eff": out}
+            ts, amps, step_ms = [0], [lat.observables([(1, 0)])["amp"][0]], 0.0
+            for k in range(T // every):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                lat.step(every)
+                e1.record(st)
+                torch.cuda.synchronize(dev)
+                step_ms += e0.elapsed_time(e1)
+                ts.append((k + 1) * every)
+                amps.append(lat.observables([(1, 0)])["amp"][0])
+        oj, om = B.lb_rates(cfg["omega_eff"])
+        with B.LB(omega_j=oj, omega=om, stream=st, **cfg) as lb:
+            lb.init()
+            lb.step(T)
+            a_lb = float(lb.observables([(1, 0)])["amp"][0])
+        ts, amps = np.array(ts, dtype=float), np.array(amps)
+        sel = ts >= 100
+        (slope, icpt), cov = np.polyfit(ts[sel], np.log(amps[sel]), 1, cov=True)
+        D_theory = cfg["theta"] * (1.0 / oj - 0.5)
+        rho = cfg["n0"] * 5
+        out[str(cfg["omega_eff"])] = {
+            "value": cfg["Lx"] * cfg["Ly"] * T / (step_ms / 1e3) / 1e9, "unit": "GNUPS", "ms_per_step": step_ms / T,
+            "kernel": tun["choice"],
+            "diffusion": {"fitted": float(-slope / k2), "stderr": float(math.sqrt(cov[0, 0]) / k2),
+                          "theory": D_theory, "fit": f"ln A^LG(t), t in [100, {T}], every {every} steps"},
+            "amplitude": {"t0": float(amps[0]), "t_end": float(amps[-1]), "lb_mean_t_end": a_lb,
+                          "sd_single_sample": math.sqrt(2.0 * rho / (cfg["Lx"] * cfg["Ly"]))}}
+    return {"workload": "sweep_d2q5: D2Q5 1024x1024, Poisson mean 50 per velocity + sine amplitude 20, "
+                        "1000 steps per omega_eff (0.5, 1.0, 1.5, 1.9)", "omega_eff": out}
+
+
+def measure_ring(torch, B, dev):
+    """The D1Q3 ring workload as stated: L = 256, mean 30 per velocity + a sine of
+    amplitude 10, omega_eff 1.5, 2000 steps, the full state and the mode-1 amplitude
+    after every step.  Through ilg_batch_run_record (one ring held in shared memory
+    for all steps, the states and amplitudes recorded on the device, one copy to the
+    host; wall clock of the whole call), and through one context stepping once per
+    call with the state and the amplitude read back after every step."""
+    cfg = {k: v for k, v in inputs.RING_D1Q3.items() if k != "steps"}
+    T = inputs.RING_D1Q3["steps"]
+    L = cfg["Lx"]
+    st = torch.cuda.Stream(dev)
+    with B.Batch([cfg], stream=st) as bat:
+        bat.init()
+        bat.run_record(T)          # graph capture and the record's allocation
+        bat.init()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        amp, states = bat.run_record(T, 1)
+        wall = time.perf_counter() - t0
+    lat_s = []
+    with B.Lattice(**cfg, stream=st) as lat:
+        lat.init()
+        buf = np.empty(lat.shape, dtype=np.uint16)
+        for _ in range(T):
+            t0 = time.perf_counter()
+            lat.step(1)
+            a_ctx = lat.observables([(1, 0)])["amp"][0]
+            lat.get_state(buf)
+            lat_s.append(time.perf_counter() - t0)
+    same = bool(np.array_equal(states[0][-1], buf)) and bool(abs(a_ctx - amp[0][-1]) <= 1e-12 * max(1.0, abs(a_ctx)))
+    lat_s = np.array(lat_s)
+    return {"workload": f"ring_d1q3: D1Q3 ring L={L}, Poisson mean 30 per velocity + sine amplitude 10, omega_eff 1.5, "
+                        f"{T} steps, state and A^LG of mode 1 after every step",
+            "value": L * T / wall / 1e9, "unit": "GNUPS", "latency_per_step_us": 1e6 * wall / T,
+            "call_s": wall, "path": "ilg_batch_run_record (wall clock, host copy of the 3 MB record included)",
+            "one_context_one_step_per_call": {
+                "value": L * T / lat_s.sum() / 1e9, "unit": "GNUPS",
+                "latency_us": {"p50": float(1e6 * np.percentile(lat_s, 50)), "p99": float(1e6 * np.percentile(lat_s, 99))}},
+            "amplitude": {"t1": float(amp[0][0]), "t_end": float(amp[0][-1])}, "identical_results": same}
 
 
 def measure_d2q9(torch, B, dev, side):
@@ -403,33 +509,33 @@ def latency_summary(res):
             {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))})
 
 
-def measure_serving(B, n_requests=200):
+def measure_serving(torch, B, dev, n_requests=200):
     """Poisson arrivals (200/s) of D2Q5 requests, submitted in real time: every
     request admitted at once (arrival order), and least-work-first admission into 32
-    slots."""
+    slots; against the same requests run one after another, one context each (created
+    and initialised outside the timing, each request's steps timed with CUDA events),
+    at identical results (mass and A^LG of every request)."""
     reqs = inputs.serve_requests(n_requests)
     tot = sum(r["Lx"] * r["Ly"] * r["steps"] for r in reqs)
     res, wall, st = serve_stream(B, reqs, 512, False)
     lat_all, queue_all = latency_summary(res)
     res2, wall2, st2 = serve_stream(B, reqs, 32, True)
     lat_sm, queue_sm = latency_summary(res2)
-    # the same subset (every 4th request) served together and run one after another,
-    # one context each, at identical results
-    sub = reqs[::4]
-    sub_nu = sum(r["Lx"] * r["Ly"] * r["steps"] for r in sub)
-    with B.Server(5, 48 << 30, max_slots=512, quantum=32) as srv:
-        t0 = time.perf_counter()
-        for i, r in enumerate(sub):
-            srv.submit(i, **{k: v for k, v in r.items() if k != "arrive"})
-        srv.wait_idle(1800)
-        served_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for r in sub:
-        with B.Lattice(**{k: v for k, v in r.items() if k not in ("arrive", "steps")}) as one:
+    served = {r["id"]: r for r in res}
+    stream = torch.cuda.Stream(dev)
+    plain_ms, same = 0.0, True
+    for i, r in enumerate(reqs):
+        with B.Lattice(**{k: v for k, v in r.items() if k not in ("arrive", "steps")}, stream=stream) as one:
             one.init()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
             one.step(r["steps"])
-            one.observables([(1, 0)])
-    plain_s = time.perf_counter() - t0
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            plain_ms += a.elapsed_time(b)
+            o = one.observables([(1, 0)])
+            same &= bool(served[i]["mass"] == o["mass"]) and bool(served[i]["amp"] == o["amp"][0])
     return {"workload": f"serve_d2q5: {n_requests} requests, Poisson arrivals 200/s, side log-uniform [64, 2048], "
                         "steps log-uniform [100, 10000], n0 uniform [5, 100], omega_eff 1.5",
             "aggregate": {"value": tot / wall / 1e9, "unit": "GNUPS"}, "offered_node_updates": tot,
@@ -438,10 +544,12 @@ def measure_serving(B, n_requests=200):
             "least_work_first_32_slots": {"aggregate": {"value": tot / wall2 / 1e9, "unit": "GNUPS"},
                                           "latency_s": lat_sm, "queueing_s": queue_sm, "completed": len(res2),
                                           "wall_s": wall2},
-            "same_subset": {"requests": "every 4th request, all submitted at once",
-                            "served": {"value": sub_nu / served_s / 1e9, "unit": "GNUPS"},
-                            "plain_one_context_per_request": {"value": sub_nu / plain_s / 1e9, "unit": "GNUPS"},
-                            "speedup": plain_s / served_s}}
+            "one_context_per_request": {
+                "value": tot / (plain_ms / 1e3) / 1e9, "unit": "GNUPS", "steps_s": plain_ms / 1e3,
+                "how": "every request alone in turn, created and initialised outside the timing, its steps timed "
+                       "with CUDA events (no arrival times: the GPU time of the plain launches alone)",
+                "identical_results": bool(same)},
+            "speedup_vs_one_context_per_request": (plain_ms / 1e3) / wall}
 
 
 def main_config(cfg, T, nmodes, world):
@@ -494,13 +602,13 @@ def main():
     ap.add_argument("--side", type=int, default=inputs.LARGE_D2Q5["Lx"], help="lattice side (default 16384)")
     ap.add_argument("--side-y", type=int, default=0, help="rows of the lattice (default: --side; profiling only)")
     ap.add_argument("--tsteps", type=int, default=inputs.LARGE_D2Q5["steps"], help="lattice steps per bench step")
-    ap.add_argument("--kernel", default="", choices=["", "vec8", "vec4", "node", "seg8"],
+    ap.add_argument("--kernel", default="", choices=["", "vec8", "vec4", "node", "seg8", "warpv8", "warpv4"],
                     help="fixed single-step kernel instead of the autotuner's choice (profiling: under ncu the "
                          "tuner's timings are not the run's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip every measurement beyond the main workload")
-    ap.add_argument("--extra", default="tb,batched,lb,ensemble,particle,d2q9,sweep,serving",
+    ap.add_argument("--extra", default="tb,batched,lb,ensemble,particle,d2q9,sweep,ring,serving",
                     help="comma-separated measurements beyond the main workload")
     ap.add_argument("--lb-side", type=int, default=0, help="side of the lattice Boltzmann workload (default 16384)")
     ap.add_argument("--batch-rings", type=int, default=4096, help="rings of the batched workload (profiling only)")
@@ -566,9 +674,6 @@ def main():
     nu = float(nodes) * T * args.steps * world
     value = nu / (total_ms / 1e3) / 1e9
     launch_ms = step_ms / (T * args.steps)
-    achieved_gbs = nodes * BYTES_PER_NU / (launch_ms / 1e3) / 1e9
-    pk = peaks()
-    peak = pk["hbm_gbs"] if pk else 6800.0
     launches = args.steps * (T + 2)
 
     e2e = None
@@ -592,6 +697,8 @@ def main():
         e2e = {"value": nu / (e_ms / 1e3) / 1e9, "unit": "GNUPS",
                "h2d_bytes_per_step": int(lat.size * 2 + 8 * len(modes)),
                "d2h_bytes_per_step": int(lat.size * 2 + 8 + 32 * len(modes))}
+
+    alu = alu_roofline(B, nodes, launch_ms, stream) if rank == 0 else None
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_modes:
@@ -624,8 +731,10 @@ def main():
             extra["d2q9"] = measure_d2q9(torch, B, dev, args.side)
         if "sweep" in parts:
             extra["sweep"] = measure_sweep(torch, B, dev)
+        if "ring" in parts:
+            extra["ring"] = measure_ring(torch, B, dev)
         if "serving" in parts:
-            extra["serving"] = measure_serving(B, args.serve_requests)
+            extra["serving"] = measure_serving(torch, B, dev, args.serve_requests)
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
@@ -654,16 +763,14 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches,
             "autotune": tuning,
-            "roofline": alu_roofline(nodes, launch_ms, clk.summary(), tuning["choice"]),
-            "hbm": {"achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
-                    "algorithmic_bytes_per_launch": nodes * BYTES_PER_NU, "peak_source": "MEASURED_PEAKS.json hbm_gbs"
-                    if pk else "fallback 6800"},
+            "roofline": hbm_roofline(nodes, launch_ms, tuning["choice"]),
+            "alu_roofline": alu,
             "observables_ms_per_step": obs_ms / args.steps,
             "cpu_baseline": cpu,
             **extra,
             "check": {"mass": obs["mass"], "t": obs["t"]},
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=json_default), flush=True)
     lat.close()
     if world > 1:
         dist.destroy_process_group()
