@@ -147,16 +147,17 @@ ilg_status ilg_set_temporal_blocking(ilg_ctx* ctx, uint32_t depth);
  *   candidate 3, 4  temporal blocking of depth 2, 4 (D2Q5; the remainder of a call
  *                takes the fastest single-step candidate)
  *   candidate 5  8-node vectors in warp segments: each warp walks 8192 nodes of a row,
- *                neighbours exchanged by shuffles, no block barrier (the default
- *                where the lattice has two segments per resident warp)
- *   candidate 6  4-node vectors in warp segments (rows a multiple of 4; both collision
+ *                neighbours exchanged by shuffles, no block barrier
+ *   candidate 6  8-node vectors in warp segments (rows a multiple of 8; both collision
  *                probabilities strictly between 0 and 1): every warp an equal share
  *                of the lattice's vectors, the next tile's occupations copied into
  *                shared memory while the current one collides, the flip a
  *                compile-time plane order, the fast collision branch-free, the
  *                values crossing a segment's ends written by the warp that computes
- *                them (no node computed twice); one block of 768 threads per SM
- *   candidate 7  as 6 with one block of 512 threads per SM
+ *                them (no node computed twice); one block of 384 threads per SM
+ *                (the default where it applies)
+ *   candidate 7  as 6 with 4-node vectors (rows a multiple of 4), 768 threads per SM
+ *                (the default where 6 does not apply and 7 does)
  * Candidates that do not apply (row length, D2Q9, occupations that need the general
  * collision) are skipped (ms_per_step < 0).  A choice that stops applying after
  * ilg_set_state (e.g. occupations rise) falls back to the default.  trial_steps:

@@ -82,7 +82,7 @@ class Tuning(ctypes.Structure):
                 ("n", ctypes.c_uint32), ("ms_per_step", ctypes.c_double * 8)]
 
 
-CONTEXT_CANDIDATES = ("vec8", "vec4", "node", "tb2", "tb4", "seg8", "warp768", "warp512")
+CONTEXT_CANDIDATES = ("vec8", "vec4", "node", "tb2", "tb4", "seg8", "warpv8", "warpv4")
 BATCH_CANDIDATES = ("threads256", "threads512", "threads1024")
 
 
@@ -236,8 +236,8 @@ class Lattice:
 
     def set_step_kernel(self, candidate: int):
         """ilg_set_step_kernel: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, 5 warp
-        segments of 8-node vectors, 6 / 7 warp segments of 4-node vectors (one block of 768 /
-        512 threads per SM), -1 default."""
+        segments of 8-node vectors, 6 / 7 the shared-memory-staged warp kernel with 8 / 4
+        nodes per lane, -1 default."""
         _check(_lib.ilg_set_step_kernel(self._h, int(candidate)), self._h)
 
     def set_temporal_blocking(self, depth: int):

@@ -109,9 +109,9 @@ void round_keys(uint64_t seed, uint32_t* rk) {
 namespace {
 using ilg::validate_params;
 
-// node-parallel kernels: `per_sm` resident blocks of 256 threads on every SM
-int step_grid(const ilg_ctx* c, size_t per_sm) {
-  const size_t blocks = (c->nodes + 255) / 256;
+// node-parallel kernels: `per_sm` resident blocks of `threads` threads on every SM
+int step_grid(const ilg_ctx* c, size_t per_sm, size_t threads = 256) {
+  const size_t blocks = (c->nodes + threads - 1) / threads;
   const size_t cap = size_t(c->sms) * per_sm;
   return int(blocks < cap ? blocks : cap);
 }
@@ -357,7 +357,7 @@ namespace {
 
 // Single-step kernels, numbered as the autotuner's candidates (3 and 4 are the
 // temporal-blocking depths).
-enum : int { kKernelVec8 = 0, kKernelVec4 = 1, kKernelNode = 2, kKernelSeg = 5, kKernelWarp768 = 6, kKernelWarp512 = 7 };
+enum : int { kKernelVec8 = 0, kKernelVec4 = 1, kKernelNode = 2, kKernelSeg = 5, kKernelWarp8 = 6, kKernelWarp4 = 7 };
 constexpr int kCandidates = 8;
 
 bool is_single_step(int cand) { return cand <= kKernelNode || (cand >= kKernelSeg && cand < kCandidates); }
@@ -365,9 +365,9 @@ bool is_single_step(int cand) { return cand <= kKernelNode || (cand >= kKernelSe
 bool kernel_applies(const ilg_ctx* c, const StepArgs& a, int kind) {
   if (kind == kKernelNode) return true;
   if (c->Q == 9 || a.general) return false;  // D2Q9 and the general path run node-parallel
-  if (kind == kKernelWarp768 || kind == kKernelWarp512) {
+  if (kind == kKernelWarp8 || kind == kKernelWarp4) {
     // whole vectors per row; the fast collision draws both probabilities through tables
-    return c->p.Lx % step_warp_width(kind == kKernelWarp512 ? 1 : 0) == 0 && a.omega_mode == kTable &&
+    return c->p.Lx % step_warp_width(kind == kKernelWarp4 ? 1 : 0) == 0 && a.omega_mode == kTable &&
            a.rest_mode == kTable;
   }
   return c->p.Lx % (kind == kKernelVec4 ? 4u : 8u) == 0;
@@ -377,10 +377,13 @@ bool kernel_applies(const ilg_ctx* c, const StepArgs& a, int kind) {
 uint64_t vec_warps(const ilg_ctx* c) { return uint64_t(c->sms) * 3 * 8; }
 
 // the kernel a step runs: the tuned one while it applies to the current state, else
-// the default: warp segments where the lattice has at least two segments per
-// resident warp, 8-node row tiles where the rows allow, node-parallel otherwise
+// the default: the shared-memory-staged warp kernel with 8-node, else 4-node vectors
+// where the rows and probabilities allow; else 8-node row tiles where the rows allow;
+// node-parallel otherwise
 int pick_kernel(const ilg_ctx* c, const StepArgs& a) {
   if (c->kernel_choice >= 0 && kernel_applies(c, a, c->kernel_choice)) return c->kernel_choice;
+  if (kernel_applies(c, a, kKernelWarp8)) return kKernelWarp8;
+  if (kernel_applies(c, a, kKernelWarp4)) return kKernelWarp4;
   if (!kernel_applies(c, a, kKernelVec8)) return kKernelNode;
   return step_seg_units(c->p.Lx, c->p.Ly) >= 2 * vec_warps(c) ? kKernelSeg : kKernelVec8;
 }
@@ -404,13 +407,14 @@ cudaError_t launch_single(const ilg_ctx* c, int kind, const StepArgs& a, const u
     const uint64_t blocks = (step_seg_units(c->p.Lx, c->p.Ly) + 7) / 8, cap = vec_warps(c) / 8;
     return launch_step_seg(c->Q, a, in, out, uint32_t(t), fail_word, int(blocks < cap ? blocks : cap), c->stream);
   }
-  if (kind == kKernelWarp768 || kind == kKernelWarp512) {
-    const int shape = kind == kKernelWarp512 ? 1 : 0;
+  if (kind == kKernelWarp8 || kind == kKernelWarp4) {
+    const int shape = kind == kKernelWarp4 ? 1 : 0;
     const uint32_t Ly = c->Q == 3 ? 1u : c->p.Ly;
     return launch_step_warp(c->Q, shape, a, in, out, uint32_t(t), fail_word,
                             int(step_warp_grid(c->p.Lx, Ly, uint32_t(c->sms), shape)), c->stream);
   }
-  return launch_step(c->Q, a, in, out, uint32_t(t), fail_word, step_grid(c, 4), c->stream);
+  return launch_step(c->Q, a, in, out, uint32_t(t), fail_word,
+                     step_grid(c, step_kernel_blocks_per_sm(), step_kernel_threads()), c->stream);
 }
 
 int tb_grid(const ilg_ctx* c, uint32_t depth) {
@@ -518,8 +522,8 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
     return cuda_fail(c, e, "autotune scratch");
   }
   // candidates: 0 8-node vectors, 1 4-node vectors, 2 node-parallel, 3 / 4 temporal
-  // blocking of depth 2 / 4 (D2Q5), 5 warp segments of 8-node vectors, 6 / 7 warp
-  // segments of 4-node vectors in one block of 768 / 512 threads per SM
+  // blocking of depth 2 / 4 (D2Q5), 5 warp segments of 8-node vectors, 6 / 7 the
+  // shared-memory-staged warp kernel with 8 / 4 nodes per lane
   ilg_tuning res{};
   res.n = kCandidates;
   for (int k = 0; k < 8; ++k) res.ms_per_step[k] = -1.0;

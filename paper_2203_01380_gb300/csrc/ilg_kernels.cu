@@ -3,6 +3,8 @@
 // projections of the observables, and a Philox probe.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "ilg_device.cuh"
 #include "ilg_launch.h"
 
@@ -11,15 +13,18 @@ namespace ilg {
 // --------------------------------------------------------------------------
 // step: one thread per node, any extent.  Loads the Q occupations of its node,
 // flips, collides and scatters n'_i to the neighbour x + v_i (periodic).
-// The lattice's two alias tables, packed one word per column, are staged in shared
-// memory once per block, beside 20 extension words per thread for the general
-// collision.  A block returns without work when an earlier launch recorded an
-// overflow.
+// The lattice's two alias tables (packed one word per column, or as {threshold,
+// alias} pairs) are staged in shared memory once per block, beside 20 extension
+// words per thread for the general collision.  A block returns without work when an
+// earlier launch recorded an overflow.
 // --------------------------------------------------------------------------
 constexpr int kStepThreads = 256;
-
-// (four blocks per SM: 32 KB of packed tables and 20 KB of extension words each)
 constexpr int kStepBlocksPerSm = 4;
+// packed tables (32 KB, one word per column) leave room for four blocks per SM; the
+// pair form (64 KB) saves two instructions per draw
+constexpr bool kStepPairTables = false;
+using StepTab = std::conditional_t<kStepPairTables, Alias8, Alias4>;
+constexpr uint32_t kStepTableWords = kStepPairTables ? kDevStagedWords : kDevTableWords4;
 
 template <int Q>
 __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(StepArgs a, const uint16_t* __restrict__ in,
@@ -28,9 +33,15 @@ __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(St
   extern __shared__ uint4 smem4[];
   __shared__ int skip;
   uint32_t* s = reinterpret_cast<uint32_t*>(smem4);
-  uint32_t* xb = s + kDevTableWords4 + threadIdx.x;  // this thread's extension words
+  uint32_t* xb = s + kStepTableWords + threadIdx.x;  // this thread's extension words
   if (threadIdx.x == 0) skip = (*reinterpret_cast<volatile unsigned long long*>(fail) != ~0ull);
-  stage_tables4(a.tables, s, a.particle != 0);  // packed: room for the extension words
+  if constexpr (kStepPairTables) {
+    // the block's first words: the pair tables, or the particle sampler's boundaries
+    const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
+    for (uint32_t i = threadIdx.x; i < kDevStagedWords / 4; i += blockDim.x) smem4[i] = g4[i];
+  } else {
+    stage_tables4(a.tables, s, a.particle != 0);
+  }
   __syncthreads();
   if (skip) return;
 
@@ -55,8 +66,8 @@ __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(St
       m[3] = a.flip ? n[4] : n[3];
       m[4] = a.flip ? n[3] : n[4];
     }
-    if (a.general || !collide_try_fast<Q, Alias4>(a, s, node, t, m, post)) {
-      collide_general<Q, kExtWords, kStepThreads, Alias4>(a, s, node, t, m, post, xb);
+    if (a.general || !collide_try_fast<Q, StepTab>(a, s, node, t, m, post)) {
+      collide_general<Q, kExtWords, kStepThreads, StepTab>(a, s, node, t, m, post, xb);
 #pragma unroll
       for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
     }
@@ -76,13 +87,16 @@ __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(St
   if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
 }
 
-constexpr size_t kStepSmem = sizeof(uint32_t) * (kDevTableWords4 + kExtWords * kStepThreads);
+constexpr size_t kStepSmem = sizeof(uint32_t) * (kStepTableWords + kExtWords * kStepThreads);
 
 cudaError_t prepare_step_kernels() {
   cudaError_t e = cudaFuncSetAttribute(step_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStepSmem));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(step_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStepSmem));
 }
+
+uint32_t step_kernel_threads() { return kStepThreads; }
+uint32_t step_kernel_blocks_per_sm() { return kStepBlocksPerSm; }
 
 cudaError_t launch_step(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                         unsigned long long* fail, int grid, cudaStream_t s) {

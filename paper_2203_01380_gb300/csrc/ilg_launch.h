@@ -23,6 +23,8 @@ struct InitArgs {
 };
 
 cudaError_t prepare_step_kernels();  // opt in to the table block's shared memory
+uint32_t step_kernel_threads();       // block shape of the node-parallel step
+uint32_t step_kernel_blocks_per_sm();
 cudaError_t launch_step(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                         unsigned long long* fail, int grid, cudaStream_t s);
 cudaError_t prepare_step_vec_kernels();
@@ -36,9 +38,10 @@ cudaError_t launch_step_vec(int Q, const StepArgs& a, const uint16_t* in, uint16
 uint64_t step_seg_units(uint32_t Lx, uint32_t Ly);
 cudaError_t launch_step_seg(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                             unsigned long long* fail, int grid, cudaStream_t s);
-// warp segments of 4-node vectors (ilg_step_warp.cu): rows a multiple of 4, both
-// probabilities drawn through tables; shape 0 = one block of 768 threads per SM,
-// shape 1 = one block of 512 threads; step_warp_grid = blocks of a launch
+// warp segments of staged vectors (ilg_step_warp.cu): rows a multiple of the width,
+// both probabilities drawn through tables; shape 0 = 8 nodes per lane, one block of
+// 384 threads per SM, shape 1 = 4 nodes per lane, 768 threads; step_warp_grid =
+// blocks of a launch
 cudaError_t prepare_step_warp_kernels();
 uint32_t step_warp_width(int shape);  // nodes per lane (rows must be a multiple)
 uint32_t step_warp_grid(uint32_t Lx, uint32_t Ly, uint32_t sms, int shape);

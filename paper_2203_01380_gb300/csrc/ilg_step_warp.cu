@@ -1,11 +1,11 @@
-// Warp-segment fused step with 4-node vectors, shaped for integer issue.
+// Warp-segment fused step with 8- or 4-node vectors, shaped for integer issue.
 //
 // The step's time goes to the integer work of its random numbers (two Philox
-// blocks and six alias draws per node), so this kernel spends its registers on
-// resident warps rather than on wide vectors or on data in flight:
-//  - each lane owns a vector of 4 consecutive nodes (8-byte accesses; a warp
-//    covers 128 nodes of a row per tile); the next tile's occupations are copied
-//    into the warp's shared-memory buffer by cp.async while the current tile
+// blocks and six alias draws per node), so this kernel spends its registers on the
+// independent work of wide vectors in few warps rather than on data in flight:
+//  - each lane owns a vector of NPT consecutive nodes (16- or 8-byte accesses; a
+//    warp covers 32 NPT nodes of a row per tile); the next tile's occupations are
+//    copied into the warp's shared-memory buffer by cp.async while the current tile
 //    collides, so the copy holds no registers;
 //  - the flip is a compile-time choice of which plane is loaded as which
 //    velocity, so it costs nothing;
@@ -35,14 +35,20 @@ namespace {
 // NPT consecutive nodes of one plane: node k in the low (k even) or high (k odd)
 // half of word k / 2
 template <int NPT>
-struct __align__(2 * NPT) VN {
+struct __align__(2 * NPT < 16 ? 2 * NPT : 16) VN {
+  static_assert(NPT == 4 || NPT == 8 || NPT == 16, "vectors of 4, 8 or 16 nodes (8-byte or 16-byte copies)");
   uint32_t w[NPT / 2];
 };
 
 template <int NPT>
 __device__ __forceinline__ void stv(uint16_t* p, const uint32_t (&w)[NPT / 2]) {
-  if constexpr (NPT == 8) *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
-  else *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+  if constexpr (NPT >= 8) {
+#pragma unroll
+    for (int j = 0; j < NPT / 8; ++j)
+      reinterpret_cast<uint4*>(p)[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+  } else {
+    *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+  }
 }
 template <int NPT>
 __device__ __forceinline__ uint32_t node_of(const VN<NPT>& v, int k) {
@@ -203,12 +209,16 @@ __device__ __forceinline__ void segment_at(uint32_t g, uint32_t end, uint32_t vp
 template <int Q, bool FLIP, int NPT>
 __device__ __forceinline__ void stage_tile(VN<NPT>* tb, const uint16_t* __restrict__ in, size_t plane, size_t rowoff,
                                            uint32_t v, bool active, uint32_t lane) {
+  constexpr int kBytes = 2 * NPT < 16 ? 2 * NPT : 16;  // per copy
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     // the flip F_i(n) = n_{-i}: velocity i of the collision reads plane -i
     const int src = !FLIP || i == 0 ? i : (i & 1 ? i + 1 : i - 1);
     const uint16_t* p = active ? in + src * plane + rowoff + size_t(v) * NPT : in;
-    cp_async<2 * NPT>(tb + i * 32 + lane, p, active);
+#pragma unroll
+    for (int c = 0; c < 2 * NPT / kBytes; ++c)
+      cp_async<kBytes>(reinterpret_cast<char*>(tb + i * 32 + lane) + c * kBytes, active ? p + c * (kBytes / 2) : p,
+                       active);
   }
   cp_async_commit();
 }
@@ -354,21 +364,24 @@ __global__ void __launch_bounds__(THREADS, MINB)
 }
 
 // Shapes (the autotuner's two candidates): one block per SM, so the 64 staged table
-// rows exist once per SM; kNpt nodes per lane, kThreads threads.  Fewer warps with
-// room for their registers beat more warps that spill (measured).
+// rows exist once per SM; kNpt nodes per lane, kThreads threads, a multiple of 128 so
+// that the four sub-partitions of an SM hold equally many warps.  Few warps with room
+// for all their registers beat more warps that spill (measured on the 16384^2
+// lattice: 8 nodes per lane, 12 warps at up to 168 registers each, 150 G node
+// updates/s; 4 nodes per lane, 24 warps at 80 registers, 135).
 constexpr int kRows = 64;
 template <int SHAPE>
 struct WarpShape;
 template <>
 struct WarpShape<0> {
-  static constexpr int kNpt = 4;
-  static constexpr int kThreads = 768;
+  static constexpr int kNpt = 8;
+  static constexpr int kThreads = 384;
   static constexpr int kBlocks = 1;
 };
 template <>
 struct WarpShape<1> {
   static constexpr int kNpt = 4;
-  static constexpr int kThreads = 512;
+  static constexpr int kThreads = 768;
   static constexpr int kBlocks = 1;
 };
 

@@ -47,7 +47,7 @@ def test_autotune_keeps_state_and_results(B):
         tun = lat.autotune(6)
         after, t1 = lat.get_state()
         assert t0 == t1 == 3 and np.array_equal(before, after)
-        assert set(tun["ms_per_step"]) == {"vec8", "vec4", "node", "tb2", "tb4", "seg8", "warp768", "warp512"}
+        assert set(tun["ms_per_step"]) == {"vec8", "vec4", "node", "tb2", "tb4", "seg8", "warpv8", "warpv4"}
         assert all(v is not None and v > 0 for v in tun["ms_per_step"].values())
         assert tun["ms_per_step"][tun["choice"]] == min(tun["ms_per_step"].values())
         lat.step(9)
@@ -57,15 +57,15 @@ def test_autotune_keeps_state_and_results(B):
 
 @pytest.mark.parametrize("cfg,applicable", [
     (dict(lattice=1, Lx=1028, n0=10.0), {"vec8": False, "vec4": True, "node": True, "tb2": False, "tb4": False,
-                                         "seg8": False, "warp768": True, "warp512": True}),
+                                         "seg8": False, "warpv8": False, "warpv4": True}),
     (dict(lattice=3, Lx=64, Ly=32, n0=10.0), {"vec8": False, "vec4": False, "node": True, "tb2": False, "tb4": False,
-                                              "seg8": False, "warp768": False, "warp512": False}),
+                                              "seg8": False, "warpv8": False, "warpv4": False}),
     (dict(lattice=2, Lx=64, Ly=32, n0=80.0), {"vec8": False, "vec4": False, "node": True, "tb2": True, "tb4": True,
-                                              "seg8": False, "warp768": False, "warp512": False}),
+                                              "seg8": False, "warpv8": False, "warpv4": False}),
     (dict(lattice=2, Lx=1024, Ly=24, n0=10.0), {"vec8": True, "vec4": True, "node": True, "tb2": True, "tb4": True,
-                                               "seg8": True, "warp768": True, "warp512": True}),
+                                               "seg8": True, "warpv8": True, "warpv4": True}),
     (dict(lattice=2, Lx=1020, Ly=6, n0=10.0), {"vec8": False, "vec4": True, "node": True, "tb2": True, "tb4": True,
-                                              "seg8": False, "warp768": True, "warp512": True}),
+                                              "seg8": False, "warpv8": False, "warpv4": True}),
 ])
 def test_autotune_candidates(B, cfg, applicable):
     with B.Lattice(omega_eff=1.5, seed=2, **cfg) as lat:
