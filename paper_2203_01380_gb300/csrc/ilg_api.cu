@@ -364,12 +364,14 @@ bool is_single_step(int cand) { return cand <= kKernelNode || (cand >= kKernelSe
 
 bool kernel_applies(const ilg_ctx* c, const StepArgs& a, int kind) {
   if (kind == kKernelNode) return true;
-  if (c->Q == 9 || a.general) return false;  // D2Q9 and the general path run node-parallel
+  if (a.general) return false;  // the general path runs node-parallel
   if (kind == kKernelWarp8 || kind == kKernelWarp4) {
-    // whole vectors per row; the fast collision draws both probabilities through tables
-    return c->p.Lx % step_warp_width(kind == kKernelWarp4 ? 1 : 0) == 0 && a.omega_mode == kTable &&
-           a.rest_mode == kTable;
+    // whole vectors per row; the fast collision draws every probability through its
+    // table (D2Q9: the axis share too)
+    return c->p.Lx % step_warp_width(c->Q, kind == kKernelWarp4 ? 1 : 0) == 0 && a.omega_mode == kTable &&
+           a.rest_mode == kTable && (c->Q != 9 || a.axis_mode == kTable);
   }
+  if (c->Q == 9) return false;  // the row-tiled register kernels: D1Q3 and D2Q5 only
   return c->p.Lx % (kind == kKernelVec4 ? 4u : 8u) == 0;
 }
 
@@ -390,7 +392,7 @@ int pick_kernel(const ilg_ctx* c, const StepArgs& a) {
 
 cudaError_t launch_single(const ilg_ctx* c, int kind, const StepArgs& a, const uint16_t* in, uint16_t* out,
                           uint64_t t, unsigned long long* fail_word) {
-  if (c->Q == 9) {
+  if (c->Q == 9 && kind != kKernelWarp8 && kind != kKernelWarp4) {
     // rows of even length run two neighbouring nodes per thread (launch_step9)
     const size_t work = c->p.Lx % 2 == 0 ? c->nodes / 2 : c->nodes;
     const size_t blocks = (work + step9_threads() - 1) / step9_threads();
@@ -411,7 +413,7 @@ cudaError_t launch_single(const ilg_ctx* c, int kind, const StepArgs& a, const u
     const int shape = kind == kKernelWarp4 ? 1 : 0;
     const uint32_t Ly = c->Q == 3 ? 1u : c->p.Ly;
     return launch_step_warp(c->Q, shape, a, in, out, uint32_t(t), fail_word,
-                            int(step_warp_grid(c->p.Lx, Ly, uint32_t(c->sms), shape)), c->stream);
+                            int(step_warp_grid(c->Q, c->p.Lx, Ly, uint32_t(c->sms), shape)), c->stream);
   }
   return launch_step(c->Q, a, in, out, uint32_t(t), fail_word,
                      step_grid(c, step_kernel_blocks_per_sm(), step_kernel_threads()), c->stream);
@@ -555,7 +557,6 @@ ilg_status ilg_autotune(ilg_ctx* c, uint32_t trial_steps, ilg_tuning* out) {
   };
   for (int cand = 0; cand < kCandidates && e == cudaSuccess; ++cand) {
     if (is_single_step(cand) && !kernel_applies(c, a, cand)) continue;
-    if (is_single_step(cand) && c->Q == 9 && cand != kKernelNode) continue;
     if (!is_single_step(cand)) {
       if (c->Q != 5) continue;
       const uint32_t depth = cand == 3 ? 2u : 4u;

@@ -39,12 +39,13 @@ uint64_t step_seg_units(uint32_t Lx, uint32_t Ly);
 cudaError_t launch_step_seg(int Q, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                             unsigned long long* fail, int grid, cudaStream_t s);
 // warp segments of staged vectors (ilg_step_warp.cu): rows a multiple of the width,
-// both probabilities drawn through tables; shape 0 = 8 nodes per lane, one block of
-// 384 threads per SM, shape 1 = 4 nodes per lane, 768 threads; step_warp_grid =
+// every probability drawn through its table; D1Q3 and D2Q5: shape 0 = 8 nodes per
+// lane, one block of 384 threads per SM, shape 1 = 4 nodes per lane, 768 threads;
+// D2Q9: 4 nodes per lane, 384 (shape 0) or 256 (shape 1) threads; step_warp_grid =
 // blocks of a launch
 cudaError_t prepare_step_warp_kernels();
-uint32_t step_warp_width(int shape);  // nodes per lane (rows must be a multiple)
-uint32_t step_warp_grid(uint32_t Lx, uint32_t Ly, uint32_t sms, int shape);
+uint32_t step_warp_width(int Q, int shape);  // nodes per lane (rows must be a multiple)
+uint32_t step_warp_grid(int Q, uint32_t Lx, uint32_t Ly, uint32_t sms, int shape);
 cudaError_t launch_step_warp(int Q, int shape, const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t,
                              unsigned long long* fail, int grid, cudaStream_t s);
 size_t step_tb_smem_bytes(uint32_t B, uint32_t Tb);

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 
+#include "ilg_d2q9.cuh"
 #include "ilg_device.cuh"
 #include "ilg_launch.h"
 
@@ -116,18 +117,62 @@ __device__ __forceinline__ uint32_t fast_draws(const uint2* to, const uint2* tr,
   return fail;
 }
 
-// The slot words of a node's step: words 0..7 of its tag-1 stream (two Philox blocks).
-__device__ __forceinline__ void slot_words(const StepArgs& a, uint32_t node, uint32_t t, uint32_t (&W)[8]) {
-  const uint4 b0 = philox_rk(counter(node, t, a.replica, kDevTagStep | 0u), a.rk);
-  const uint4 b1 = philox_rk(counter(node, t, a.replica, kDevTagStep | 1u), a.rk);
-  W[0] = b0.x;
-  W[1] = b0.y;
-  W[2] = b0.z;
-  W[3] = b0.w;
-  W[4] = b1.x;
-  W[5] = b1.y;
-  W[6] = b1.z;
-  W[7] = b1.w;
+// The slot words of a node's step: words 0..4 NB - 1 of its tag-1 stream (NB Philox
+// blocks: two for D1Q3 and D2Q5, four for D2Q9).
+template <int NB>
+__device__ __forceinline__ void slot_words(const StepArgs& a, uint32_t node, uint32_t t, uint32_t (&W)[4 * NB]) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const uint4 w = philox_rk(counter(node, t, a.replica, kDevTagStep | uint32_t(b)), a.rk);
+    W[4 * b] = w.x;
+    W[4 * b + 1] = w.y;
+    W[4 * b + 2] = w.z;
+    W[4 * b + 3] = w.w;
+  }
+}
+
+// D2Q9 fast collision of one node whose occupations are all below ROWS, branch-free
+// (the fast path of ilg_d2q9.cuh with the same words and results): thinning W0..W8,
+// rest W9, axis share W10, axis particles (A, B) = (W11, W12), diagonal particles
+// (X, Y) = (W13, W14).  Nonzero when the node needs the general collision (more than
+// ROWS - 1 removed, more than 32 axis or diagonal movers).
+template <int ROWS>
+__device__ __forceinline__ uint32_t fast_draws9(const uint2* to, const uint2* tr, const uint2* ta,
+                                                const uint32_t (&W)[16], const uint32_t (&m)[9], uint32_t (&out)[9]) {
+  uint32_t r[9];
+  uint32_t removed = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    r[i] = draw(to, m[i], W[i]);
+    removed += r[i];
+  }
+  uint32_t fail = removed >= uint32_t(ROWS) ? 1u : 0u;
+  const uint32_t rr = min(removed, uint32_t(ROWS - 1));
+  const uint32_t to_rest = draw(tr, rr, W[9]);
+  const uint32_t moving = rr - to_rest;
+  const uint32_t axis = draw(ta, moving, W[10]);
+  const uint32_t diag = moving - axis;
+  fail |= (axis > 32u || diag > 32u) ? 1u : 0u;
+  const uint32_t ma = __funnelshift_lc(0xFFFFFFFFu, 0u, axis);  // (1 << c) - 1, c <= 32
+  const uint32_t md = __funnelshift_lc(0xFFFFFFFFu, 0u, diag);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) out[i] = m[i] - r[i];
+  out[0] += to_rest;
+  // axis particles: axis bit A (0: x, 1: y), sign bit B (0: +, 1: -)
+  const uint32_t A = W[11] & ma, B = W[12] & ma;
+  const uint32_t ny = __popc(A), nmy = __popc(A & B), nmx = __popc(B & ~A);
+  out[1] += axis - ny - nmx;
+  out[2] += nmx;
+  out[3] += ny - nmy;
+  out[4] += nmy;
+  // diagonal particles: x-sign bit X, y-sign bit Y (0: +, 1: -)
+  const uint32_t X = W[13] & md, Y = W[14] & md;
+  const uint32_t nmm = __popc(X & Y), npm = __popc(Y) - nmm, nmp = __popc(X) - nmm;
+  out[5] += diag - nmm - npm - nmp;
+  out[6] += nmm;
+  out[7] += npm;
+  out[8] += nmp;
+  return fail;
 }
 
 // The general collision of the nodes of a vector marked in `slow`, out of line; the
@@ -143,7 +188,8 @@ __device__ __noinline__ bool slow_nodes(const StepArgs& a, const uint32_t* gt, u
     uint32_t m[Q], o[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) m[i] = node_of(N[i], k);
-    collide<Q>(a, gt, node0 + k, t, m, o);
+    if constexpr (Q == 9) collide9_general(a, gt, node0 + k, t, m, o);
+    else collide<Q>(a, gt, node0 + k, t, m, o);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       bad |= o[i] > 65535u;
@@ -159,16 +205,16 @@ __device__ __noinline__ bool slow_nodes(const StepArgs& a, const uint32_t* gt, u
 // post-collision planes P.  N holds the vector's occupations with the flip already
 // applied (plane i loaded from the flipped source).
 template <int Q, int ROWS, int NPT>
-__device__ __forceinline__ void collide_vec(const StepArgs& a, const uint2* to, const uint2* tr, uint32_t node0,
-                                            uint32_t t, VN<NPT> (&N)[Q], VN<NPT> (&P)[Q], bool& bad) {
+__device__ __forceinline__ void collide_vec(const StepArgs& a, const uint2* to, const uint2* tr, const uint2* ta,
+                                            uint32_t node0, uint32_t t, VN<NPT> (&N)[Q], VN<NPT> (&P)[Q], bool& bad) {
   constexpr uint32_t kHigh = ROWS == 32 ? 0xFFE0FFE0u : 0xFFC0FFC0u;  // bits of values >= ROWS
   uint32_t any = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i)
 #pragma unroll
     for (int j = 0; j < NPT / 2; ++j) any |= N[i].w[j];
-  // the fast collision needs both probabilities drawn through their tables
-  if (a.omega_mode != kTable || a.rest_mode != kTable) any = 0xFFFFFFFFu;
+  // the fast collision needs every probability drawn through its table
+  if (a.omega_mode != kTable || a.rest_mode != kTable || (Q == 9 && a.axis_mode != kTable)) any = 0xFFFFFFFFu;
   uint32_t slow = (any & kHigh) ? (1u << NPT) - 1u : 0u;
 #pragma unroll
   for (int i = 0; i < Q; ++i)
@@ -180,9 +226,15 @@ __device__ __forceinline__ void collide_vec(const StepArgs& a, const uint2* to, 
       uint32_t m[Q], o[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) m[i] = node_of(N[i], k);
-      uint32_t W[8];
-      slot_words(a, node0 + k, t, W);
-      slow |= fast_draws<Q, ROWS>(to, tr, W, m, o) << k;
+      if constexpr (Q == 9) {
+        uint32_t W[16];
+        slot_words<4>(a, node0 + k, t, W);
+        slow |= fast_draws9<ROWS>(to, tr, ta, W, m, o) << k;
+      } else {
+        uint32_t W[8];
+        slot_words<2>(a, node0 + k, t, W);
+        slow |= fast_draws<Q, ROWS>(to, tr, W, m, o) << k;
+      }
       // pack the node's results into its half-words as soon as they exist
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -223,6 +275,18 @@ __device__ __forceinline__ void stage_tile(VN<NPT>* tb, const uint16_t* __restri
   cp_async_commit();
 }
 
+// Velocity i's displacement (dx, dy) in the storage order of each lattice.
+template <int Q>
+__device__ __forceinline__ constexpr int vel_dx(int i) {
+  return Q == 9 ? ((i == 1 || i == 5 || i == 7) ? 1 : ((i == 2 || i == 6 || i == 8) ? -1 : 0))
+                : (i == 1 ? 1 : (i == 2 ? -1 : 0));
+}
+template <int Q>
+__device__ __forceinline__ constexpr int vel_dy(int i) {
+  return Q == 9 ? ((i == 3 || i == 5 || i == 8) ? 1 : ((i == 4 || i == 6 || i == 7) ? -1 : 0))
+                : (Q == 5 ? (i == 3 ? 1 : (i == 4 ? -1 : 0)) : 0);
+}
+
 template <int Q, bool FLIP, int ROWS, int NPT, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
     step_warp_kernel(const __grid_constant__ StepArgs a, const uint16_t* __restrict__ in,
@@ -230,17 +294,20 @@ __global__ void __launch_bounds__(THREADS, MINB)
   extern __shared__ uint4 smem4[];
   __shared__ int skip;
   if (threadIdx.x == 0) skip = (*reinterpret_cast<const volatile unsigned long long*>(fail) != ~0ull);
+  constexpr uint32_t kTables = Q == 9 ? 3 : 2;           // thinning, rest (D2Q9: and the axis share)
   constexpr uint32_t kRow4 = ROWS * kDevAliasCols / 2;  // uint4 per staged table
   {
-    // rows 0..ROWS-1 of the thinning and the rest alias tables (uint2 entries, two per uint4)
+    // rows 0..ROWS-1 of each alias table (uint2 entries, two per uint4)
     const uint4* g4 = reinterpret_cast<const uint4*>(a.tables);
     constexpr uint32_t kTab4 = kDevAliasEntries / 2;  // uint4 per full table
-    for (uint32_t i = threadIdx.x; i < 2 * kRow4; i += THREADS) smem4[i] = g4[i < kRow4 ? i : kTab4 + (i - kRow4)];
+    for (uint32_t i = threadIdx.x; i < kTables * kRow4; i += THREADS)
+      smem4[i] = g4[(i / kRow4) * kTab4 + (i % kRow4)];
   }
   __syncthreads();
   if (skip) return;
   const uint2* to = reinterpret_cast<const uint2*>(smem4);
   const uint2* tr = to + ROWS * kDevAliasCols;
+  const uint2* ta = tr + ROWS * kDevAliasCols;  // D2Q9 only
 
   constexpr unsigned kFull = 0xFFFFFFFFu;
   constexpr int H = NPT / 2;  // words per vector
@@ -249,7 +316,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
   const uint32_t vpr = Lx / NPT;
   const uint32_t lane = threadIdx.x & 31u;
   // this warp's two tile buffers (Q planes of 32 vectors each) after the tables
-  VN<NPT>* tbuf = reinterpret_cast<VN<NPT>*>(smem4 + 2 * kRow4) + (threadIdx.x >> 5) * (2 * Q * 32);
+  VN<NPT>* tbuf = reinterpret_cast<VN<NPT>*>(smem4 + kTables * kRow4) + (threadIdx.x >> 5) * (2 * Q * 32);
   // this warp's share of the row-major sequence of all vectors: [g, end)
   const uint64_t total = uint64_t(vpr) * Ly, nwarps = (uint64_t(gridDim.x) * THREADS) >> 5;
   const uint64_t w = (uint64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5;
@@ -263,8 +330,21 @@ __global__ void __launch_bounds__(THREADS, MINB)
   uint32_t vb = v0;
   int buf = 0;
   stage_tile<Q, FLIP, NPT>(tbuf, in, plane, size_t(y) * Lx, vb + lane, vb + lane < v1, lane);
-  uint32_t carry = 0;  // +x value of the previous tile's lane 31
-  VN<NPT> held_mx{};   // lane 31: -x vector waiting for the next tile's first node
+  uint32_t carry[Q];   // +x planes: the value of the previous tile's lane 31
+  VN<NPT> held[Q];     // -x planes, lane 31: the vector waiting for the next tile's first node
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    carry[i] = 0;
+    held[i] = VN<NPT>{};
+  }
+  // [p1 .. p_{NPT-1}, r]: a -x vector with r for its last slot
+  auto shift_down = [](const VN<NPT>& p, uint32_t r) {
+    VN<NPT> o;
+#pragma unroll
+    for (int j = 0; j < H - 1; ++j) o.w[j] = __byte_perm(p.w[j], p.w[j + 1], 0x5432);
+    o.w[H - 1] = __byte_perm(p.w[H - 1], r, 0x5432);
+    return o;
+  };
   while (true) {
     // the next tile: of this segment, or the first of the segment that follows it;
     // its copies are queued before this tile collides
@@ -283,74 +363,103 @@ __global__ void __launch_bounds__(THREADS, MINB)
 #pragma unroll
     for (int i = 0; i < Q; ++i) cur[i] = tbuf[buf * (Q * 32) + i * 32 + lane];
 
-    const size_t rowoff = size_t(y) * Lx;
     const uint32_t v = vb + lane;
     const bool active = v < v1;
     const uint32_t x0 = v * NPT;
     VN<NPT> P[Q];
-    collide_vec<Q, ROWS, NPT>(a, to, tr, uint32_t(rowoff) + x0, t, cur, P, bad);
+    collide_vec<Q, ROWS, NPT>(a, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, cur, P, bad);
+    const uint32_t yp = y + 1 == Ly ? 0 : y + 1;
+    const uint32_t ym = y == 0 ? Ly - 1 : y - 1;
+    // streaming: velocity i lands in row y + dy of its plane, shifted by dx within it
+    auto row_of = [&](int i) {
+      const int dy = vel_dy<Q>(i);
+      return out + i * plane + size_t(dy == 0 ? y : (dy > 0 ? yp : ym)) * Lx;
+    };
     if (active) {
-      stv<NPT>(out + rowoff + x0, P[0].w);
-      if constexpr (Q == 5) {
-        const uint32_t yp = y + 1 == Ly ? 0 : y + 1;
-        const uint32_t ym = y == 0 ? Ly - 1 : y - 1;
-        stv<NPT>(out + 3 * plane + size_t(yp) * Lx + x0, P[3].w);
-        stv<NPT>(out + 4 * plane + size_t(ym) * Lx + x0, P[4].w);
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        if (vel_dx<Q>(i) == 0) stv<NPT>(row_of(i) + x0, P[i].w);
+    }
+    // +x planes: each node's value moves one node right (the left neighbour's last
+    // node); -x planes: one node left (the right neighbour's first node)
+    uint32_t left[Q], right[Q], tile_first[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (vel_dx<Q>(i) > 0) {
+        const uint32_t last = P[i].w[H - 1] >> 16;
+        left[i] = __shfl_up_sync(kFull, last, 1);
+        if (lane == 0) left[i] = carry[i];
+        carry[i] = __shfl_sync(kFull, last, 31);
+      } else if (vel_dx<Q>(i) < 0) {
+        const uint32_t first = P[i].w[0] & 0xFFFFu;
+        right[i] = __shfl_down_sync(kFull, first, 1);
+        tile_first[i] = __shfl_sync(kFull, first, 0);
       }
     }
-    // +x: each node's value moves one node right; the left neighbour's last node
-    const uint32_t last_px = P[1].w[H - 1] >> 16;
-    uint32_t left = __shfl_up_sync(kFull, last_px, 1);
-    if (lane == 0) left = carry;
-    carry = __shfl_sync(kFull, last_px, 31);
-    // -x: one node left; the right neighbour's first node
-    const uint32_t first_mx = P[2].w[0] & 0xFFFFu;
-    const uint32_t right = __shfl_down_sync(kFull, first_mx, 1);
-    const uint32_t tile_first = __shfl_sync(kFull, first_mx, 0);
-    uint16_t* const px = out + plane + rowoff;
-    uint16_t* const mx = out + 2 * plane + rowoff;
-    // [p1 .. p_{NPT-1}, r]: the -x vector with r for its last slot
-    auto shift_down = [&](const VN<NPT>& p, uint32_t r) {
-      VN<NPT> o;
+    if (lane == 31 && vb > v0) {
 #pragma unroll
-      for (int j = 0; j < H - 1; ++j) o.w[j] = __byte_perm(p.w[j], p.w[j + 1], 0x5432);
-      o.w[H - 1] = __byte_perm(p.w[H - 1], r, 0x5432);
-      return o;
-    };
-    if (lane == 31 && vb > v0) stv<NPT>(mx + (vb - 1) * NPT, shift_down(held_mx, tile_first).w);
+      for (int i = 0; i < Q; ++i)
+        if (vel_dx<Q>(i) < 0) stv<NPT>(row_of(i) + (vb - 1) * NPT, shift_down(held[i], tile_first[i]).w);
+    }
     if (active) {
       const bool seg_first = v == v0, seg_last = v + 1 == v1;
       if (!seg_first) {
-        // [l, p0 .. p_{NPT-2}]
-        uint32_t o[H];
-        o[0] = __byte_perm(left, P[1].w[0], 0x5410);
 #pragma unroll
-        for (int j = 1; j < H; ++j) o[j] = __byte_perm(P[1].w[j - 1], P[1].w[j], 0x5432);
-        stv<NPT>(px + x0, o);
+        for (int i = 0; i < Q; ++i) {
+          if (vel_dx<Q>(i) > 0) {
+            // [l, p0 .. p_{NPT-2}]
+            uint32_t o[H];
+            o[0] = __byte_perm(left[i], P[i].w[0], 0x5410);
+#pragma unroll
+            for (int j = 1; j < H; ++j) o[j] = __byte_perm(P[i].w[j - 1], P[i].w[j], 0x5432);
+            stv<NPT>(row_of(i) + x0, o);
+          }
+        }
       } else {
-        // the segment's first +x slot belongs to the node left of the segment
-        px[x0 + 1] = uint16_t(P[1].w[0]);
 #pragma unroll
-        for (int j = 1; j < H; ++j)
-          *reinterpret_cast<uint32_t*>(px + x0 + 2 * j) = __byte_perm(P[1].w[j - 1], P[1].w[j], 0x5432);
-        // and this node's -x value belongs to that node's slot
-        mx[x0 == 0 ? Lx - 1 : x0 - 1] = uint16_t(P[2].w[0]);
+        for (int i = 0; i < Q; ++i) {
+          uint16_t* const row = row_of(i);
+          if (vel_dx<Q>(i) > 0) {
+            // the segment's first +x slot belongs to the node left of the segment
+            row[x0 + 1] = uint16_t(P[i].w[0]);
+#pragma unroll
+            for (int j = 1; j < H; ++j)
+              *reinterpret_cast<uint32_t*>(row + x0 + 2 * j) = __byte_perm(P[i].w[j - 1], P[i].w[j], 0x5432);
+          } else if (vel_dx<Q>(i) < 0) {
+            // and this node's -x value belongs to that node's slot
+            row[x0 == 0 ? Lx - 1 : x0 - 1] = uint16_t(P[i].w[0]);
+          }
+        }
       }
       if (seg_last) {
-        px[x0 + NPT == Lx ? 0 : x0 + NPT] = uint16_t(P[1].w[H - 1] >> 16);
 #pragma unroll
-        for (int j = 0; j < H - 1; ++j)
-          *reinterpret_cast<uint32_t*>(mx + x0 + 2 * j) = __byte_perm(P[2].w[j], P[2].w[j + 1], 0x5432);
-        mx[x0 + NPT - 2] = uint16_t(P[2].w[H - 1] >> 16);
+        for (int i = 0; i < Q; ++i) {
+          uint16_t* const row = row_of(i);
+          if (vel_dx<Q>(i) > 0) {
+            // the segment's last +x value belongs to the first slot of the next segment
+            row[x0 + NPT == Lx ? 0 : x0 + NPT] = uint16_t(P[i].w[H - 1] >> 16);
+          } else if (vel_dx<Q>(i) < 0) {
+            // [p1 .. p_{NPT-1}]: the last -x slot belongs to the node right of the segment
+#pragma unroll
+            for (int j = 0; j < H - 1; ++j)
+              *reinterpret_cast<uint32_t*>(row + x0 + 2 * j) = __byte_perm(P[i].w[j], P[i].w[j + 1], 0x5432);
+            row[x0 + NPT - 2] = uint16_t(P[i].w[H - 1] >> 16);
+          }
+        }
       } else if (lane < 31) {
-        stv<NPT>(mx + x0, shift_down(P[2], right).w);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          if (vel_dx<Q>(i) < 0) stv<NPT>(row_of(i) + x0, shift_down(P[i], right[i]).w);
       } else {
-        held_mx = P[2];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          if (vel_dx<Q>(i) < 0) held[i] = P[i];
       }
     }
     if (!more) break;
     if (!same) {
-      carry = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) carry[i] = 0;
       g = g_next;
       y = ny;
       v0 = nv0;
@@ -385,16 +494,34 @@ struct WarpShape<1> {
   static constexpr int kBlocks = 1;
 };
 
+// D2Q9 (nine planes, four Philox blocks and eleven draws per node): 4 nodes per lane
+// in 384 or 256 threads
+template <int Q, int SHAPE>
+struct WarpShapeQ : WarpShape<SHAPE> {};
+template <>
+struct WarpShapeQ<9, 0> {
+  static constexpr int kNpt = 4;
+  static constexpr int kThreads = 384;
+  static constexpr int kBlocks = 1;
+};
+template <>
+struct WarpShapeQ<9, 1> {
+  static constexpr int kNpt = 4;
+  static constexpr int kThreads = 256;
+  static constexpr int kBlocks = 1;
+};
+
 // tables, then two tile buffers of Q planes x 32 vectors per warp
 template <int Q, int SHAPE>
 constexpr size_t warp_smem() {
-  using S = WarpShape<SHAPE>;
-  return sizeof(uint2) * 2 * kRows * kDevAliasCols + size_t(S::kThreads / 32) * 2 * Q * 32 * (2 * S::kNpt);
+  using S = WarpShapeQ<Q, SHAPE>;
+  return sizeof(uint2) * (Q == 9 ? 3 : 2) * kRows * kDevAliasCols +
+         size_t(S::kThreads / 32) * 2 * Q * 32 * (2 * S::kNpt);
 }
 
 template <int Q, bool FLIP, int SHAPE>
 constexpr auto warp_kernel() {
-  using S = WarpShape<SHAPE>;
+  using S = WarpShapeQ<Q, SHAPE>;
   return step_warp_kernel<Q, FLIP, kRows, S::kNpt, S::kThreads, S::kBlocks>;
 }
 
@@ -411,9 +538,27 @@ cudaError_t warp_attr() {
 template <int Q, int SHAPE>
 void warp_launch(const StepArgs& a, const uint16_t* in, uint16_t* out, uint32_t t, unsigned long long* fail, int grid,
                  cudaStream_t s) {
-  constexpr int kThreads = WarpShape<SHAPE>::kThreads;
+  constexpr int kThreads = WarpShapeQ<Q, SHAPE>::kThreads;
   if (a.flip) warp_kernel<Q, true, SHAPE>()<<<grid, kThreads, warp_smem<Q, SHAPE>(), s>>>(a, in, out, t, fail);
   else warp_kernel<Q, false, SHAPE>()<<<grid, kThreads, warp_smem<Q, SHAPE>(), s>>>(a, in, out, t, fail);
+}
+
+template <int Q>
+void shape_of(int shape, uint32_t* npt, uint32_t* threads, uint32_t* per_sm) {
+  if (shape == 1) {
+    *npt = WarpShapeQ<Q, 1>::kNpt;
+    *threads = WarpShapeQ<Q, 1>::kThreads;
+    *per_sm = WarpShapeQ<Q, 1>::kBlocks;
+  } else {
+    *npt = WarpShapeQ<Q, 0>::kNpt;
+    *threads = WarpShapeQ<Q, 0>::kThreads;
+    *per_sm = WarpShapeQ<Q, 0>::kBlocks;
+  }
+}
+
+void shape_of(int Q, int shape, uint32_t* npt, uint32_t* threads, uint32_t* per_sm) {
+  if (Q == 9) shape_of<9>(shape, npt, threads, per_sm);
+  else shape_of<5>(shape, npt, threads, per_sm);
 }
 
 }  // namespace
@@ -423,18 +568,24 @@ cudaError_t prepare_step_warp_kernels() {
   if (e == cudaSuccess) e = warp_attr<3, 1>();
   if (e == cudaSuccess) e = warp_attr<5, 0>();
   if (e == cudaSuccess) e = warp_attr<5, 1>();
+  if (e == cudaSuccess) e = warp_attr<9, 0>();
+  if (e == cudaSuccess) e = warp_attr<9, 1>();
   return e;
 }
 
-uint32_t step_warp_width(int shape) { return shape == 1 ? WarpShape<1>::kNpt : WarpShape<0>::kNpt; }
+uint32_t step_warp_width(int Q, int shape) {
+  uint32_t npt, threads, per_sm;
+  shape_of(Q, shape, &npt, &threads, &per_sm);
+  return npt;
+}
 
 // Blocks of a launch: one per SM, or fewer on lattices too small to give each warp
 // at least four tiles.
-uint32_t step_warp_grid(uint32_t Lx, uint32_t Ly, uint32_t sms, int shape) {
-  const int threads = shape == 1 ? WarpShape<1>::kThreads : WarpShape<0>::kThreads;
-  const int per_sm = shape == 1 ? WarpShape<1>::kBlocks : WarpShape<0>::kBlocks;
+uint32_t step_warp_grid(int Q, uint32_t Lx, uint32_t Ly, uint32_t sms, int shape) {
+  uint32_t npt, threads, per_sm;
+  shape_of(Q, shape, &npt, &threads, &per_sm);
   const uint64_t cap = uint64_t(sms) * per_sm;
-  const uint64_t warps = std::max<uint64_t>(1, uint64_t(Lx / step_warp_width(shape)) * Ly / 128);
+  const uint64_t warps = std::max<uint64_t>(1, uint64_t(Lx / npt) * Ly / 128);
   return uint32_t(std::min<uint64_t>(cap, (warps + threads / 32 - 1) / (threads / 32)));
 }
 
@@ -443,9 +594,12 @@ cudaError_t launch_step_warp(int Q, int shape, const StepArgs& a, const uint16_t
   if (Q == 3) {
     if (shape == 1) warp_launch<3, 1>(a, in, out, t, fail, grid, s);
     else warp_launch<3, 0>(a, in, out, t, fail, grid, s);
-  } else {
+  } else if (Q == 5) {
     if (shape == 1) warp_launch<5, 1>(a, in, out, t, fail, grid, s);
     else warp_launch<5, 0>(a, in, out, t, fail, grid, s);
+  } else {
+    if (shape == 1) warp_launch<9, 1>(a, in, out, t, fail, grid, s);
+    else warp_launch<9, 0>(a, in, out, t, fail, grid, s);
   }
   return cudaGetLastError();
 }

@@ -58,8 +58,13 @@ def test_autotune_keeps_state_and_results(B):
 @pytest.mark.parametrize("cfg,applicable", [
     (dict(lattice=1, Lx=1028, n0=10.0), {"vec8": False, "vec4": True, "node": True, "tb2": False, "tb4": False,
                                          "seg8": False, "warpv8": False, "warpv4": True}),
-    (dict(lattice=3, Lx=64, Ly=32, n0=10.0), {"vec8": False, "vec4": False, "node": True, "tb2": False, "tb4": False,
-                                              "seg8": False, "warpv8": False, "warpv4": False}),
+    (dict(lattice=3, Lx=64, Ly=32, n0=6.0), {"vec8": False, "vec4": False, "node": True, "tb2": False, "tb4": False,
+                                              "seg8": False, "warpv8": True, "warpv4": True}),
+    (dict(lattice=3, Lx=66, Ly=8, n0=6.0), {"vec8": False, "vec4": False, "node": True, "tb2": False, "tb4": False,
+                                             "seg8": False, "warpv8": False, "warpv4": False}),
+    (dict(lattice=3, Lx=64, Ly=8, n0=6.0, sampler=1), {"vec8": False, "vec4": False, "node": True, "tb2": False,
+                                                        "tb4": False, "seg8": False, "warpv8": False,
+                                                        "warpv4": False}),
     (dict(lattice=2, Lx=64, Ly=32, n0=80.0), {"vec8": False, "vec4": False, "node": True, "tb2": True, "tb4": True,
                                               "seg8": False, "warpv8": False, "warpv4": False}),
     (dict(lattice=2, Lx=1024, Ly=24, n0=10.0), {"vec8": True, "vec4": True, "node": True, "tb2": True, "tb4": True,

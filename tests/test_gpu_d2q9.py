@@ -60,6 +60,31 @@ def test_steps_bit_exact(B, Lx, Ly, omega, theta, mean, hot, sampler):
     assert t == 29 and np.array_equal(got, O.Lattice(**cfg).run(s0, 21, 8))
 
 
+@pytest.mark.parametrize("kernel", [2, 6, 7])
+@pytest.mark.parametrize("Lx,Ly,omega,theta,mean,hot,hot_value", [
+    (96, 40, 1.8, 1 / 3, 10.0, 3, 900),   # several tiles per row; nodes for the general collision
+    (100, 23, 0.7, 0.45, 5.0, 6, 60),     # ragged last tile; no flip; nodes whose removals pass 63
+    (2056, 9, 1.3, 1 / 3, 6.0, 1, 900),   # segments split at row ends across warps
+    (8200, 3, 1.6, 0.45, 9.0, 0, 0),      # long rows, few of them
+    (4, 5, 1.7, 1 / 3, 12.0, 0, 0),       # one vector per row: both its ends wrap
+    (36, 3, 0.9, 0.3, 4.0, 1, 60),        # three rows: every diagonal wraps
+])
+def test_step_kernels_bit_exact(B, kernel, Lx, Ly, omega, theta, mean, hot, hot_value):
+    """The node-parallel D2Q9 step (candidate 2) and the staged warp step with
+    4-node vectors in 384 or 256 threads (candidates 6, 7) give the oracle's bits."""
+    s0 = inputs.random_state(9, Ly, Lx, mean, seed=Lx + 7 * Ly, hot=hot, hot_value=hot_value)
+    # mean removals per node low enough for the lattice to keep its fast-path kernels
+    omega_star = 2.0 - omega if omega > 1.0 else omega
+    assert omega_star * 9 * s0.mean() <= 40.0
+    cfg = dict(lattice=3, Lx=Lx, Ly=Ly, omega_eff=omega, theta=theta, seed=17, replica=3)
+    with B.Lattice(**cfg) as lat:
+        lat.set_step_kernel(kernel)
+        lat.set_state(s0, 5)
+        lat.step(7)
+        got, t = lat.get_state()
+    assert t == 12 and np.array_equal(got, O.Lattice(**cfg).run(s0, 5, 7))
+
+
 def test_observables_and_overflow(B):
     cfg = dict(lattice=3, Lx=30, Ly=22, n0=12.0, amp=40.0, mode_mx=2, init_weighted=1, omega_eff=1.3, seed=4)
     ref = O.Lattice(**cfg)
