@@ -175,27 +175,29 @@ __device__ __forceinline__ uint32_t fast_draws9(const uint2* to, const uint2* tr
   return fail;
 }
 
-// The general collision of the nodes of a vector marked in `slow`, out of line; the
-// results overwrite their half-words of P.  gt: the full Alias8 tables in global
-// memory.  Returns true when a result exceeds 65535.
+// The general collision of the nodes of a vector marked in `slow`, out of line.  N:
+// the lane's slot of the current tile buffer in shared memory (plane i at N[32 i],
+// flip applied); node k's results are written to half-word k of R[32 i] (the lane's
+// slot of the warp's scratch in shared memory).  Both live in shared memory so that
+// no register array of the caller has its address taken (which would keep it in
+// local memory on every tile).  gt: the full Alias8 tables in global memory.
+// Returns true when a result exceeds 65535.
 template <int Q, int NPT>
 __device__ __noinline__ bool slow_nodes(const StepArgs& a, const uint32_t* gt, uint32_t node0, uint32_t t,
-                                        const VN<NPT>* N, VN<NPT>* P, uint32_t slow) {
+                                        const VN<NPT>* N, VN<NPT>* R, uint32_t slow) {
   bool bad = false;
   while (slow) {
     const int k = __ffs(slow) - 1;
     slow &= slow - 1;
     uint32_t m[Q], o[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) m[i] = node_of(N[i], k);
+    for (int i = 0; i < Q; ++i) m[i] = node_of(N[32 * i], k);
     if constexpr (Q == 9) collide9_general(a, gt, node0 + k, t, m, o);
     else collide<Q>(a, gt, node0 + k, t, m, o);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       bad |= o[i] > 65535u;
-      const uint32_t v = o[i] & 0xFFFFu;
-      uint32_t& w = P[i].w[k >> 1];
-      w = (k & 1) ? ((w & 0x0000FFFFu) | (v << 16)) : ((w & 0xFFFF0000u) | v);
+      reinterpret_cast<uint16_t*>(&R[32 * i])[k] = uint16_t(o[i]);
     }
   }
   return bad;
@@ -206,7 +208,8 @@ __device__ __noinline__ bool slow_nodes(const StepArgs& a, const uint32_t* gt, u
 // applied (plane i loaded from the flipped source).
 template <int Q, int ROWS, int NPT>
 __device__ __forceinline__ void collide_vec(const StepArgs& a, const uint2* to, const uint2* tr, const uint2* ta,
-                                            uint32_t node0, uint32_t t, VN<NPT> (&N)[Q], VN<NPT> (&P)[Q], bool& bad) {
+                                            uint32_t node0, uint32_t t, const VN<NPT> (&N)[Q], VN<NPT> (&P)[Q],
+                                            const VN<NPT>* slot, VN<NPT>* scratch, bool& bad) {
   constexpr uint32_t kHigh = ROWS == 32 ? 0xFFE0FFE0u : 0xFFC0FFC0u;  // bits of values >= ROWS
   uint32_t any = 0;
 #pragma unroll
@@ -243,7 +246,19 @@ __device__ __forceinline__ void collide_vec(const StepArgs& a, const uint2* to, 
       }
     }
   }
-  if (slow) bad |= slow_nodes<Q, NPT>(a, a.tables, node0, t, N, P, slow);
+  if (slow) {
+    bad |= slow_nodes<Q, NPT>(a, a.tables, node0, t, slot, scratch, slow);
+    // take the general collision's half-words for the nodes it redid
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const VN<NPT> r = scratch[32 * i];
+#pragma unroll
+      for (int j = 0; j < NPT / 2; ++j) {
+        const uint32_t mask = ((slow >> (2 * j)) & 1u ? 0x0000FFFFu : 0u) | ((slow >> (2 * j + 1)) & 1u ? 0xFFFF0000u : 0u);
+        P[i].w[j] = (P[i].w[j] & ~mask) | (r.w[j] & mask);
+      }
+    }
+  }
 }
 
 // The segment that starts at vector g of the row-major sequence of all vectors
@@ -317,6 +332,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
   const uint32_t lane = threadIdx.x & 31u;
   // this warp's two tile buffers (Q planes of 32 vectors each) after the tables
   VN<NPT>* tbuf = reinterpret_cast<VN<NPT>*>(smem4 + kTables * kRow4) + (threadIdx.x >> 5) * (2 * Q * 32);
+  // this lane's slot of the warp's scratch for the general collision's results (after
+  // all tile buffers)
+  VN<NPT>* const scratch = reinterpret_cast<VN<NPT>*>(smem4 + kTables * kRow4) + (THREADS / 32) * (2 * Q * 32) +
+                           (threadIdx.x >> 5) * (Q * 32) + lane;
   // this warp's share of the row-major sequence of all vectors: [g, end)
   const uint64_t total = uint64_t(vpr) * Ly, nwarps = (uint64_t(gridDim.x) * THREADS) >> 5;
   const uint64_t w = (uint64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5;
@@ -367,7 +386,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
     const bool active = v < v1;
     const uint32_t x0 = v * NPT;
     VN<NPT> P[Q];
-    collide_vec<Q, ROWS, NPT>(a, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, cur, P, bad);
+    collide_vec<Q, ROWS, NPT>(a, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, cur, P,
+                              tbuf + buf * (Q * 32) + lane, scratch, bad);
     const uint32_t yp = y + 1 == Ly ? 0 : y + 1;
     const uint32_t ym = y == 0 ? Ly - 1 : y - 1;
     // streaming: velocity i lands in row y + dy of its plane, shifted by dx within it
@@ -511,12 +531,13 @@ struct WarpShapeQ<9, 1> {
   static constexpr int kBlocks = 1;
 };
 
-// tables, then two tile buffers of Q planes x 32 vectors per warp
+// tables, then two tile buffers of Q planes x 32 vectors per warp, then one scratch
+// buffer of the same shape per warp
 template <int Q, int SHAPE>
 constexpr size_t warp_smem() {
   using S = WarpShapeQ<Q, SHAPE>;
   return sizeof(uint2) * (Q == 9 ? 3 : 2) * kRows * kDevAliasCols +
-         size_t(S::kThreads / 32) * 2 * Q * 32 * (2 * S::kNpt);
+         size_t(S::kThreads / 32) * 3 * Q * 32 * (2 * S::kNpt);
 }
 
 template <int Q, bool FLIP, int SHAPE>
