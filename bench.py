@@ -185,7 +185,7 @@ def oracle_all_cores(cfg, side, steps, seconds):
 KERNEL_NAMES = {"vec8": "step_vec_kernel<5, 8>", "vec4": "step_vec_kernel<5, 4>", "node": "step_kernel<5>",
                 "tb2": "step_tb_kernel (depth 2)", "tb4": "step_tb_kernel (depth 4)", "seg8": "step_seg_kernel<5, 8>",
                 "warpv8": "step_warp_kernel<5, flip, 64 rows, 8 nodes per lane, 384 threads>",
-                "warpv4": "step_warp_kernel<5, flip, 64 rows, 4 nodes per lane, 768 threads>"}
+                "warpv4": "step_warp_kernel<5, flip, 64 rows, 4 nodes per lane, 640 threads>"}
 
 
 def hbm_roofline(nodes, launch_ms, choice):
@@ -470,8 +470,8 @@ def measure_d2q9(torch, B, dev, side):
     nodes = side * side
     pk = peaks()
     hpk = pk["hbm_gbs"] if pk else 6800.0
-    names = {6: "step_warp_kernel<9>, 4-node vectors, 384 threads per SM (default)",
-             7: "step_warp_kernel<9>, 4-node vectors, 256 threads per SM",
+    names = {6: "step_warp_kernel<9>, 4-node vectors, 512 threads per SM (default)",
+             7: "step_warp_kernel<9>, 4-node vectors, 384 threads per SM",
              2: "step9_pair_kernel (node-parallel, two nodes of a row per thread)"}
     kernels, obs = {}, []
     for cand in (6, 7, 2):

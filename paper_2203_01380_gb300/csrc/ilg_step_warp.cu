@@ -73,10 +73,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Binomial(n, P) for n < 64 with one draw u through the alias table A (rows of 64
 // columns, column u >> 26): the column's own outcome below its threshold, else its
-// alias.
+// alias.  HI: the column as the high word of u * 64 (a multiply, on the FMA pipe,
+// where the ALU pipe is the busier one: D2Q9) instead of a shift.
+template <bool HI = false>
 __device__ __forceinline__ uint32_t draw(const uint2* A, uint32_t n, uint32_t u) {
   const uint2 e = A[__funnelshift_l(u, n, 6)];
-  return u < e.x ? (u >> 26) : e.y;
+  return u < e.x ? (HI ? __umulhi(u, 64u) : (u >> 26)) : e.y;
 }
 
 // Fast collision of one node whose occupations are all below ROWS, branch-free, from
@@ -143,14 +145,14 @@ __device__ __forceinline__ uint32_t fast_draws9(const uint2* to, const uint2* tr
   uint32_t removed = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    r[i] = draw(to, m[i], W[i]);
+    r[i] = draw<true>(to, m[i], W[i]);
     removed += r[i];
   }
   uint32_t fail = removed >= uint32_t(ROWS) ? 1u : 0u;
   const uint32_t rr = min(removed, uint32_t(ROWS - 1));
-  const uint32_t to_rest = draw(tr, rr, W[9]);
+  const uint32_t to_rest = draw<true>(tr, rr, W[9]);
   const uint32_t moving = rr - to_rest;
-  const uint32_t axis = draw(ta, moving, W[10]);
+  const uint32_t axis = draw<true>(ta, moving, W[10]);
   const uint32_t diag = moving - axis;
   fail |= (axis > 32u || diag > 32u) ? 1u : 0u;
   const uint32_t ma = __funnelshift_lc(0xFFFFFFFFu, 0u, axis);  // (1 << c) - 1, c <= 32
@@ -495,9 +497,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
 // Shapes (the autotuner's two candidates): one block per SM, so the 64 staged table
 // rows exist once per SM; kNpt nodes per lane, kThreads threads, a multiple of 128 so
 // that the four sub-partitions of an SM hold equally many warps.  Few warps with room
-// for all their registers beat more warps that spill (measured on the 16384^2
-// lattice: 8 nodes per lane, 12 warps at up to 168 registers each, 150 G node
-// updates/s; 4 nodes per lane, 24 warps at 80 registers, 135).
+// for all their registers beat more warps that spill (measured on the 16384^2 D2Q5
+// lattice: 8 nodes per lane, 12 warps at up to 168 registers each, 153 G node
+// updates/s; 4 nodes per lane, 20 warps at up to 96 registers, 138; 24 warps at 80,
+// 133).
 constexpr int kRows = 64;
 template <int SHAPE>
 struct WarpShape;
@@ -510,24 +513,24 @@ struct WarpShape<0> {
 template <>
 struct WarpShape<1> {
   static constexpr int kNpt = 4;
-  static constexpr int kThreads = 768;
+  static constexpr int kThreads = 640;
   static constexpr int kBlocks = 1;
 };
 
 // D2Q9 (nine planes, four Philox blocks and eleven draws per node): 4 nodes per lane
-// in 384 or 256 threads
+// in 512 or 384 threads
 template <int Q, int SHAPE>
 struct WarpShapeQ : WarpShape<SHAPE> {};
 template <>
 struct WarpShapeQ<9, 0> {
   static constexpr int kNpt = 4;
-  static constexpr int kThreads = 384;
+  static constexpr int kThreads = 512;
   static constexpr int kBlocks = 1;
 };
 template <>
 struct WarpShapeQ<9, 1> {
   static constexpr int kNpt = 4;
-  static constexpr int kThreads = 256;
+  static constexpr int kThreads = 384;
   static constexpr int kBlocks = 1;
 };
 
