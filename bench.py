@@ -470,8 +470,8 @@ def measure_d2q9(torch, B, dev, side):
     nodes = side * side
     pk = peaks()
     hpk = pk["hbm_gbs"] if pk else 6800.0
-    names = {6: "step_warp_kernel<9>, 4-node vectors, 512 threads per SM (default)",
-             7: "step_warp_kernel<9>, 4-node vectors, 384 threads per SM",
+    names = {6: "step_warp_kernel<9>, 4-node vectors collided in shared memory, 512 threads per SM (default)",
+             7: "step_warp_kernel<9>, 4-node vectors collided in shared memory, 640 threads per SM",
              2: "step9_pair_kernel (node-parallel, two nodes of a row per thread)"}
     kernels, obs = {}, []
     for cand in (6, 7, 2):

@@ -160,8 +160,9 @@ ilg_status ilg_set_temporal_blocking(ilg_ctx* ctx, uint32_t depth);
  *                (the default where 6 does not apply and 7 does)
  *   D2Q9 lattices: candidate 2 (node-parallel, two nodes of a row per thread where
  *                rows are even) and the staged warp step with 4-node vectors (rows a
- *                multiple of 4; all three probabilities strictly between 0 and 1) in
- *                512 threads per SM (candidate 6) or 384 (candidate 7)
+ *                multiple of 4; all three probabilities strictly between 0 and 1),
+ *                collided two nodes at a time in shared memory, in 512 threads per SM
+ *                (candidate 6, the default where it applies) or 640 (candidate 7)
  * Candidates that do not apply (row length, lattice, occupations that need the
  * general collision, the particle sampler) are skipped (ms_per_step < 0).  A choice that stops applying after
  * ilg_set_state (e.g. occupations rise) falls back to the default.  trial_steps:

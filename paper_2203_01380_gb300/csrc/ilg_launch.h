@@ -41,7 +41,8 @@ cudaError_t launch_step_seg(int Q, const StepArgs& a, const uint16_t* in, uint16
 // warp segments of staged vectors (ilg_step_warp.cu): rows a multiple of the width,
 // every probability drawn through its table; D1Q3 and D2Q5: shape 0 = 8 nodes per
 // lane, one block of 384 threads per SM, shape 1 = 4 nodes per lane, 640 threads;
-// D2Q9: 4 nodes per lane, 512 (shape 0) or 384 (shape 1) threads; step_warp_grid =
+// D2Q9: 4 nodes per lane collided in shared memory, 512 (shape 0) or 640 (shape 1)
+// threads; step_warp_grid =
 // blocks of a launch
 cudaError_t prepare_step_warp_kernels();
 uint32_t step_warp_width(int Q, int shape);  // nodes per lane (rows must be a multiple)

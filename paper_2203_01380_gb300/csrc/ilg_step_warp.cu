@@ -19,7 +19,11 @@
 //    tile by tile, as segments that end at row ends; neighbouring lanes trade
 //    edge values by shuffles, and the two values that cross a segment's ends are
 //    written as single 16-bit stores by the warp that computes them, so no node is
-//    computed twice and no warp waits for another.
+//    computed twice and no warp waits for another;
+//  - D1Q3 and D2Q5 hold a lane's vector and its results in registers; D2Q9 (nine
+//    planes, four Philox blocks and eleven draws per node) leaves the vector in the
+//    tile buffer and collides it two nodes at a time in place, which frees the
+//    registers for more warps.
 // Every random number is keyed by node and step, so the bits equal those of every
 // other step kernel.
 #include <cuda_runtime.h>
@@ -179,11 +183,12 @@ __device__ __forceinline__ uint32_t fast_draws9(const uint2* to, const uint2* tr
 
 // The general collision of the nodes of a vector marked in `slow`, out of line.  N:
 // the lane's slot of the current tile buffer in shared memory (plane i at N[32 i],
-// flip applied); node k's results are written to half-word k of R[32 i] (the lane's
-// slot of the warp's scratch in shared memory).  Both live in shared memory so that
-// no register array of the caller has its address taken (which would keep it in
-// local memory on every tile).  gt: the full Alias8 tables in global memory.
-// Returns true when a result exceeds 65535.
+// flip applied); node k's results are written to half-word k of R[32 i]: the lane's
+// slot of the warp's scratch in shared memory, or the slot itself when the vector is
+// collided in place.  Both live in shared memory so that no register array of the
+// caller has its address taken (which would keep it in local memory on every tile).
+// gt: the full Alias8 tables in global memory.  Returns true when a result exceeds
+// 65535.
 template <int Q, int NPT>
 __device__ __noinline__ bool slow_nodes(const StepArgs& a, const uint32_t* gt, uint32_t node0, uint32_t t,
                                         const VN<NPT>* N, VN<NPT>* R, uint32_t slow) {
@@ -263,6 +268,71 @@ __device__ __forceinline__ void collide_vec(const StepArgs& a, const uint2* to, 
   }
 }
 
+// 32-bit shared-memory load and store at a shared-window address, kept in program
+// order with the other shared accesses of the lane's slots
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
+}
+
+// collide_vec with the vector left in shared memory: the nodes are taken two at a
+// time (one 32-bit word per plane) from the lane's slot of the tile buffer (plane i at
+// slot[32 i]), and their packed results replace the occupations they came from, so
+// only one pair's occupations and results are held in registers at a time.  A pair is
+// written only when both its nodes passed the fast collision; otherwise both are
+// redone by the general collision, which still finds their occupations in the slot.
+template <int Q, int ROWS, int NPT>
+__device__ __forceinline__ void collide_vec_res(const StepArgs& a, const uint2* to, const uint2* tr, const uint2* ta,
+                                                uint32_t node0, uint32_t t, VN<NPT>* slot, bool& bad) {
+  constexpr uint32_t kHigh = ROWS == 32 ? 0xFFE0FFE0u : 0xFFC0FFC0u;  // bits of values >= ROWS
+  constexpr uint32_t kPlane = 32 * sizeof(VN<NPT>);                     // bytes between planes
+  const bool tables = a.omega_mode == kTable && a.rest_mode == kTable && (Q != 9 || a.axis_mode == kTable);
+  const uint32_t sn = static_cast<uint32_t>(__cvta_generic_to_shared(slot));
+  uint32_t slow = 0;
+#pragma unroll
+  for (int j = 0; j < NPT / 2; ++j) {
+    uint32_t w[Q];
+    uint32_t any = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      w[i] = lds32(sn + i * kPlane + 4 * j);
+      any |= w[i];
+    }
+    if (!tables || (any & kHigh)) {
+      slow |= 3u << (2 * j);
+      continue;
+    }
+    uint32_t o[2][Q];
+    uint32_t f = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t m[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) m[i] = h ? (w[i] >> 16) : (w[i] & 0xFFFFu);
+      if constexpr (Q == 9) {
+        uint32_t W[16];
+        slot_words<4>(a, node0 + 2 * j + h, t, W);
+        f |= fast_draws9<ROWS>(to, tr, ta, W, m, o[h]) << h;
+      } else {
+        uint32_t W[8];
+        slot_words<2>(a, node0 + 2 * j + h, t, W);
+        f |= fast_draws<Q, ROWS>(to, tr, W, m, o[h]) << h;
+      }
+    }
+    if (f) {
+      slow |= 3u << (2 * j);
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) sts32(sn + i * kPlane + 4 * j, __byte_perm(o[0][i], o[1][i], 0x5410));
+  }
+  if (slow) bad |= slow_nodes<Q, NPT>(a, a.tables, node0, t, slot, slot, slow);
+}
+
 // The segment that starts at vector g of the row-major sequence of all vectors
 // (vpr per row) and ends at the end of its row or at end, whichever comes first:
 // row y, vectors [v0, v1) of that row.
@@ -304,7 +374,7 @@ __device__ __forceinline__ constexpr int vel_dy(int i) {
                 : (Q == 5 ? (i == 3 ? 1 : (i == 4 ? -1 : 0)) : 0);
 }
 
-template <int Q, bool FLIP, int ROWS, int NPT, int THREADS, int MINB>
+template <int Q, bool FLIP, int ROWS, int NPT, int THREADS, int MINB, bool RES>
 __global__ void __launch_bounds__(THREADS, MINB)
     step_warp_kernel(const __grid_constant__ StepArgs a, const uint16_t* __restrict__ in,
                      uint16_t* __restrict__ out, uint32_t t, unsigned long long* __restrict__ fail) {
@@ -380,16 +450,22 @@ __global__ void __launch_bounds__(THREADS, MINB)
     stage_tile<Q, FLIP, NPT>(tbuf + (buf ^ 1) * (Q * 32), in, plane, size_t(ny) * Lx, nvb + lane,
                              more && nvb + lane < nv1, lane);
     cp_async_wait_prior();
-    VN<NPT> cur[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) cur[i] = tbuf[buf * (Q * 32) + i * 32 + lane];
-
     const uint32_t v = vb + lane;
     const bool active = v < v1;
     const uint32_t x0 = v * NPT;
     VN<NPT> P[Q];
-    collide_vec<Q, ROWS, NPT>(a, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, cur, P,
-                              tbuf + buf * (Q * 32) + lane, scratch, bad);
+    if constexpr (RES) {
+      VN<NPT>* const slot = tbuf + buf * (Q * 32) + lane;
+      collide_vec_res<Q, ROWS, NPT>(a, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, slot, bad);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) P[i] = slot[32 * i];
+    } else {
+      VN<NPT> cur[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) cur[i] = tbuf[buf * (Q * 32) + i * 32 + lane];
+      collide_vec<Q, ROWS, NPT>(a, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, cur, P,
+                                tbuf + buf * (Q * 32) + lane, scratch, bad);
+    }
     const uint32_t yp = y + 1 == Ly ? 0 : y + 1;
     const uint32_t ym = y == 0 ? Ly - 1 : y - 1;
     // streaming: velocity i lands in row y + dy of its plane, shifted by dx within it
@@ -509,16 +585,21 @@ struct WarpShape<0> {
   static constexpr int kNpt = 8;
   static constexpr int kThreads = 384;
   static constexpr int kBlocks = 1;
+  static constexpr bool kRes = false;
 };
 template <>
 struct WarpShape<1> {
   static constexpr int kNpt = 4;
   static constexpr int kThreads = 640;
   static constexpr int kBlocks = 1;
+  static constexpr bool kRes = false;
 };
 
 // D2Q9 (nine planes, four Philox blocks and eleven draws per node): 4 nodes per lane
-// in 512 or 384 threads
+// left in shared memory and collided two at a time (nine planes of vectors in
+// registers would cost 36 of them), 512 or 640 threads (measured on the 16384^2
+// lattice: 70.0 and 68.9 G node updates/s; with the vectors in registers, 512
+// threads: 62.9)
 template <int Q, int SHAPE>
 struct WarpShapeQ : WarpShape<SHAPE> {};
 template <>
@@ -526,27 +607,29 @@ struct WarpShapeQ<9, 0> {
   static constexpr int kNpt = 4;
   static constexpr int kThreads = 512;
   static constexpr int kBlocks = 1;
+  static constexpr bool kRes = true;
 };
 template <>
 struct WarpShapeQ<9, 1> {
   static constexpr int kNpt = 4;
-  static constexpr int kThreads = 384;
+  static constexpr int kThreads = 640;
   static constexpr int kBlocks = 1;
+  static constexpr bool kRes = true;
 };
 
-// tables, then two tile buffers of Q planes x 32 vectors per warp, then one scratch
-// buffer of the same shape per warp
+// tables, then two tile buffers of Q planes x 32 vectors per warp, then (vectors in
+// registers only) one scratch buffer of the same shape per warp
 template <int Q, int SHAPE>
 constexpr size_t warp_smem() {
   using S = WarpShapeQ<Q, SHAPE>;
   return sizeof(uint2) * (Q == 9 ? 3 : 2) * kRows * kDevAliasCols +
-         size_t(S::kThreads / 32) * 3 * Q * 32 * (2 * S::kNpt);
+         size_t(S::kThreads / 32) * (S::kRes ? 2 : 3) * Q * 32 * (2 * S::kNpt);
 }
 
 template <int Q, bool FLIP, int SHAPE>
 constexpr auto warp_kernel() {
   using S = WarpShapeQ<Q, SHAPE>;
-  return step_warp_kernel<Q, FLIP, kRows, S::kNpt, S::kThreads, S::kBlocks>;
+  return step_warp_kernel<Q, FLIP, kRows, S::kNpt, S::kThreads, S::kBlocks, S::kRes>;
 }
 
 template <int Q, int SHAPE>
