@@ -105,6 +105,14 @@ __device__ __forceinline__ uint32_t ext_word(const StepArgs& a, ExtStream& e) {
   return w;
 }
 
+// Word e of a node's extension stream, computed alone and out of line: the rare
+// word beyond a thread's shared-memory buffer, kept out of the loops that read the
+// buffer (inlined there, its Philox rounds weigh on every iteration).
+static __device__ __noinline__ uint32_t ext_word_at(const StepArgs& a, uint32_t node, uint32_t t, uint32_t e) {
+  const uint4 b = philox_rk(counter(node, t, a.replica, kDevTagExt | (e >> 2)), a.rk);
+  return lane_of(b, e & 3u);
+}
+
 // The two alias tables of the block (shared memory).
 __device__ __forceinline__ const uint2* thinning_table(const uint32_t* s) {
   return reinterpret_cast<const uint2*>(s);
@@ -224,8 +232,10 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* s, ui
 // groups), a whole Philox block at a time, into this thread's shared-memory
 // buffer (word e at xb[e * S]; threads interleaved with stride S, so a warp's
 // accesses hit distinct banks), so a warp runs its blocks together; words beyond K
-// are read lazily.  A probability of 0 or 2^32 draws nothing.
-template <int Q, int K, int S, class Tab = Alias8>
+// are read lazily, inline, or with OOL one at a time out of line (which keeps the
+// loops that read the buffer small, where a kernel has registers for the call).  A
+// probability of 0 or 2^32 draws nothing.
+template <int Q, int K, int S, class Tab = Alias8, bool OOL = false>
 __device__ __forceinline__ void collide_buffered(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
                                                  const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
   static_assert(K % 4 == 0, "whole Philox blocks");
@@ -253,6 +263,7 @@ __device__ __forceinline__ void collide_buffered(const StepArgs& a, const uint32
   ExtStream lazy{node, t, 0u, 0xFFFFFFFFu, make_uint4(0, 0, 0, 0)};
   auto word = [&](uint32_t e) -> uint32_t {
     if (e < uint32_t(K)) return xb[e * S];
+    if constexpr (OOL) return ext_word_at(a, node, t, e);
     lazy.next = e;
     return ext_word(a, lazy);
   };
@@ -366,11 +377,11 @@ __device__ void collide_particle(const StepArgs& a, const uint32_t* s, uint32_t 
 }
 
 // The general collision in whichever sampler the lattice uses.
-template <int Q, int K, int S, class Tab = Alias8>
+template <int Q, int K, int S, class Tab = Alias8, bool OOL = false>
 __device__ __forceinline__ void collide_general(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
                                                 const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
   if (a.particle) collide_particle<Q>(a, s, node, t, m, out);
-  else collide_buffered<Q, K, S, Tab>(a, s, node, t, m, out, xb);
+  else collide_buffered<Q, K, S, Tab, OOL>(a, s, node, t, m, out, xb);
 }
 
 // The collision of one node, fast path: every occupation <= 63, at most 63

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(St
       m[4] = a.flip ? n[3] : n[4];
     }
     if (a.general || !collide_try_fast<Q, StepTab>(a, s, node, t, m, post)) {
-      collide_general<Q, kExtWords, kStepThreads, StepTab>(a, s, node, t, m, post, xb);
+      collide_general<Q, kExtWords, kStepThreads, StepTab, true>(a, s, node, t, m, post, xb);
 #pragma unroll
       for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
     }
