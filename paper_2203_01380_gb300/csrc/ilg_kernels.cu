@@ -48,10 +48,13 @@ __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(St
   const uint32_t nodes = a.Lx * a.Ly;
   const size_t plane = nodes;
   bool bad = false;
-  for (uint32_t node = blockIdx.x * blockDim.x + threadIdx.x; node < nodes;
-       node += gridDim.x * blockDim.x) {
-    const uint32_t y = node / a.Lx;
-    const uint32_t x = node - y * a.Lx;
+  // (x, y) of the node, advanced by the grid stride (stride_y rows and stride_x
+  // nodes) with a carry instead of a division per node
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t stride_y = stride / a.Lx, stride_x = stride - stride_y * a.Lx;
+  uint32_t node = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t y = node / a.Lx, x = node - y * a.Lx;
+  for (; node < nodes; node += stride) {
     uint32_t n[Q], m[Q], post[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) n[i] = in[i * plane + node];
@@ -82,6 +85,12 @@ __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(St
       const uint32_t ym = y == 0 ? a.Ly - 1 : y - 1;
       out[3 * plane + size_t(yp) * a.Lx + x] = uint16_t(post[3]);
       out[4 * plane + size_t(ym) * a.Lx + x] = uint16_t(post[4]);
+    }
+    x += stride_x;
+    y += stride_y;
+    if (x >= a.Lx) {
+      x -= a.Lx;
+      y += 1;
     }
   }
   if (bad) atomicMin(fail, static_cast<unsigned long long>(t));
