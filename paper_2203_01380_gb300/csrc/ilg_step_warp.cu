@@ -123,20 +123,6 @@ __device__ __forceinline__ uint32_t fast_draws(const uint2* to, const uint2* tr,
   return fail;
 }
 
-// The slot words of a node's step: words 0..4 NB - 1 of its tag-1 stream (NB Philox
-// blocks: two for D1Q3 and D2Q5, four for D2Q9).
-template <int NB>
-__device__ __forceinline__ void slot_words(const StepArgs& a, uint32_t node, uint32_t t, uint32_t (&W)[4 * NB]) {
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const uint4 w = philox_rk(counter(node, t, a.replica, kDevTagStep | uint32_t(b)), a.rk);
-    W[4 * b] = w.x;
-    W[4 * b + 1] = w.y;
-    W[4 * b + 2] = w.z;
-    W[4 * b + 3] = w.w;
-  }
-}
-
 // D2Q9 fast collision of one node whose occupations are all below ROWS, branch-free
 // (the fast path of ilg_d2q9.cuh with the same words and results): thinning W0..W8,
 // rest W9, axis share W10, axis particles (A, B) = (W11, W12), diagonal particles
@@ -214,9 +200,10 @@ __device__ __noinline__ bool slow_nodes(const StepArgs& a, const uint32_t* gt, u
 // post-collision planes P.  N holds the vector's occupations with the flip already
 // applied (plane i loaded from the flipped source).
 template <int Q, int ROWS, int NPT>
-__device__ __forceinline__ void collide_vec(const StepArgs& a, const uint2* to, const uint2* tr, const uint2* ta,
-                                            uint32_t node0, uint32_t t, const VN<NPT> (&N)[Q], VN<NPT> (&P)[Q],
-                                            const VN<NPT>* slot, VN<NPT>* scratch, bool& bad) {
+__device__ __forceinline__ void collide_vec(const StepArgs& a, const StepKeys<Q == 9 ? 4 : 2>& keys, const uint2* to,
+                                            const uint2* tr, const uint2* ta, uint32_t node0, uint32_t t,
+                                            const VN<NPT> (&N)[Q], VN<NPT> (&P)[Q], const VN<NPT>* slot,
+                                            VN<NPT>* scratch, bool& bad) {
   constexpr uint32_t kHigh = ROWS == 32 ? 0xFFE0FFE0u : 0xFFC0FFC0u;  // bits of values >= ROWS
   uint32_t any = 0;
 #pragma unroll
@@ -238,11 +225,11 @@ __device__ __forceinline__ void collide_vec(const StepArgs& a, const uint2* to, 
       for (int i = 0; i < Q; ++i) m[i] = node_of(N[i], k);
       if constexpr (Q == 9) {
         uint32_t W[16];
-        slot_words<4>(a, node0 + k, t, W);
+        step_blocks<4>(keys, a.rk, node0 + k, W);
         slow |= fast_draws9<ROWS>(to, tr, ta, W, m, o) << k;
       } else {
         uint32_t W[8];
-        slot_words<2>(a, node0 + k, t, W);
+        step_blocks<2>(keys, a.rk, node0 + k, W);
         slow |= fast_draws<Q, ROWS>(to, tr, W, m, o) << k;
       }
       // pack the node's results into its half-words as soon as they exist
@@ -286,8 +273,9 @@ __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
 // written only when both its nodes passed the fast collision; otherwise both are
 // redone by the general collision, which still finds their occupations in the slot.
 template <int Q, int ROWS, int NPT>
-__device__ __forceinline__ void collide_vec_res(const StepArgs& a, const uint2* to, const uint2* tr, const uint2* ta,
-                                                uint32_t node0, uint32_t t, VN<NPT>* slot, bool& bad) {
+__device__ __forceinline__ void collide_vec_res(const StepArgs& a, const StepKeys<Q == 9 ? 4 : 2>& keys,
+                                                const uint2* to, const uint2* tr, const uint2* ta, uint32_t node0,
+                                                uint32_t t, VN<NPT>* slot, bool& bad) {
   constexpr uint32_t kHigh = ROWS == 32 ? 0xFFE0FFE0u : 0xFFC0FFC0u;  // bits of values >= ROWS
   constexpr uint32_t kPlane = 32 * sizeof(VN<NPT>);                     // bytes between planes
   const bool tables = a.omega_mode == kTable && a.rest_mode == kTable && (Q != 9 || a.axis_mode == kTable);
@@ -315,11 +303,11 @@ __device__ __forceinline__ void collide_vec_res(const StepArgs& a, const uint2* 
       for (int i = 0; i < Q; ++i) m[i] = h ? (w[i] >> 16) : (w[i] & 0xFFFFu);
       if constexpr (Q == 9) {
         uint32_t W[16];
-        slot_words<4>(a, node0 + 2 * j + h, t, W);
+        step_blocks<4>(keys, a.rk, node0 + 2 * j + h, W);
         f |= fast_draws9<ROWS>(to, tr, ta, W, m, o[h]) << h;
       } else {
         uint32_t W[8];
-        slot_words<2>(a, node0 + 2 * j + h, t, W);
+        step_blocks<2>(keys, a.rk, node0 + 2 * j + h, W);
         f |= fast_draws<Q, ROWS>(to, tr, W, m, o[h]) << h;
       }
     }
@@ -415,6 +403,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
   uint32_t g = uint32_t(w * total / nwarps);
   if (g >= end) return;
   bool bad = false;
+  const StepKeys<Q == 9 ? 4 : 2> keys = step_keys<Q == 9 ? 4 : 2>(a, t);  // the launch-uniform Philox rounds
 
   uint32_t y, v0, v1;
   segment_at(g, end, vpr, y, v0, v1);
@@ -456,14 +445,14 @@ __global__ void __launch_bounds__(THREADS, MINB)
     VN<NPT> P[Q];
     if constexpr (RES) {
       VN<NPT>* const slot = tbuf + buf * (Q * 32) + lane;
-      collide_vec_res<Q, ROWS, NPT>(a, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, slot, bad);
+      collide_vec_res<Q, ROWS, NPT>(a, keys, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, slot, bad);
 #pragma unroll
       for (int i = 0; i < Q; ++i) P[i] = slot[32 * i];
     } else {
       VN<NPT> cur[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) cur[i] = tbuf[buf * (Q * 32) + i * 32 + lane];
-      collide_vec<Q, ROWS, NPT>(a, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, cur, P,
+      collide_vec<Q, ROWS, NPT>(a, keys, to, tr, ta, uint32_t(size_t(y) * Lx) + x0, t, cur, P,
                                 tbuf + buf * (Q * 32) + lane, scratch, bad);
     }
     const uint32_t yp = y + 1 == Ly ? 0 : y + 1;
