@@ -232,11 +232,21 @@ __device__ __forceinline__ void collide_vec(const StepArgs& a, const StepKeys<Q 
         step_blocks<2>(keys, a.rk, node0 + k, W);
         slow |= fast_draws<Q, ROWS>(to, tr, W, m, o) << k;
       }
-      // pack the node's results into its half-words as soon as they exist
+      // pack the node's results into its half-words as soon as they exist: an odd
+      // node's by a multiply-add (the FMA pipe: the ALU pipe is the busier one), which
+      // is exact because every fast-path result, even a failing node's, lies in
+      // [0, 126] (no draw exceeds its trials, and at most min(moving, 32) of the
+      // moving particles are sorted), so the even node's high half is zero
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         uint32_t& w = P[i].w[k >> 1];
-        w = (k & 1) ? __byte_perm(w, o[i], 0x5410) : o[i];
+        if (k & 1) {
+          uint32_t packed;
+          asm("mad.lo.u32 %0, %1, 65536, %2;\n" : "=r"(packed) : "r"(o[i]), "r"(w));
+          w = packed;
+        } else {
+          w = o[i];
+        }
       }
     }
   }
