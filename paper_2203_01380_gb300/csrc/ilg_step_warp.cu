@@ -222,7 +222,18 @@ __device__ __forceinline__ void collide_vec(const StepArgs& a, const StepKeys<Q 
     for (int k = 0; k < NPT; ++k) {
       uint32_t m[Q], o[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) m[i] = node_of(N[i], k);
+      for (int i = 0; i < Q; ++i) {
+        // the odd node is the high half; the even node the word minus it times 2^16,
+        // a multiply-add (FMA pipe) where a mask would take the busier ALU pipe
+        const uint32_t w = N[i].w[k >> 1], high = w >> 16;
+        if (k & 1) {
+          m[i] = high;
+        } else {
+          uint32_t low;
+          asm("mad.lo.u32 %0, %1, %2, %3;\n" : "=r"(low) : "r"(high), "r"(0xFFFF0000u), "r"(w));
+          m[i] = low;
+        }
+      }
       if constexpr (Q == 9) {
         uint32_t W[16];
         step_blocks<4>(keys, a.rk, node0 + k, W);
