@@ -24,9 +24,11 @@ __device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s,
                                            bool& bad, uint32_t* xb) {
   const uint32_t Lx = a.Lx, Ly = a.Ly;
   const size_t plane = size_t(Lx) * Ly;
-  for (uint32_t nd = node0 + threadIdx.x; nd < node1; nd += blockDim.x) {
-    const uint32_t y = nd / Lx;
-    const uint32_t x = nd - y * Lx;
+  // (x, y) carried across the block stride instead of a division per node
+  const uint32_t sy = blockDim.x / Lx, sx = blockDim.x - sy * Lx;
+  uint32_t nd = node0 + threadIdx.x;
+  uint32_t y = nd / Lx, x = nd - y * Lx;
+  for (; nd < node1; nd += blockDim.x) {
     const size_t row = size_t(y) * Lx;
     const size_t at = row + x;
     uint32_t n[Q], m[Q], post[Q];
@@ -55,6 +57,12 @@ __device__ __forceinline__ void step_nodes(const StepArgs& a, const uint32_t* s,
       out[3 * plane + size_t(yp) * Lx + x] = uint16_t(post[3]);
       out[4 * plane + size_t(ym) * Lx + x] = uint16_t(post[4]);
     }
+    x += sx;
+    y += sy;
+    if (x >= Lx) {
+      x -= Lx;
+      y += 1;
+    }
   }
 }
 
@@ -68,9 +76,11 @@ __device__ __forceinline__ void step_node_pairs(const StepArgs& a, const uint32_
                                                 bool& bad, uint32_t* xb) {
   const uint32_t Lx = a.Lx, Ly = a.Ly;
   const size_t plane = size_t(Lx) * Ly;
-  for (uint32_t nd = node0 + 2 * threadIdx.x; nd < node1; nd += 2 * blockDim.x) {
-    const uint32_t y = nd / Lx;
-    const uint32_t x = nd - y * Lx;  // even
+  // (x, y) carried across the block stride (x stays even: Lx and the stride are even)
+  const uint32_t sy = 2 * blockDim.x / Lx, sx = 2 * blockDim.x - sy * Lx;
+  uint32_t nd = node0 + 2 * threadIdx.x;
+  uint32_t y = nd / Lx, x = nd - y * Lx;
+  for (; nd < node1; nd += 2 * blockDim.x) {
     const size_t row = size_t(y) * Lx;
     const size_t at = row + x;
     uint32_t w[Q];
@@ -106,6 +116,12 @@ __device__ __forceinline__ void step_node_pairs(const StepArgs& a, const uint32_
       const uint32_t ym = y == 0 ? Ly - 1 : y - 1;
       *reinterpret_cast<uint32_t*>(out + 3 * plane + size_t(yp) * Lx + x) = pair(3);
       *reinterpret_cast<uint32_t*>(out + 4 * plane + size_t(ym) * Lx + x) = pair(4);
+    }
+    x += sx;
+    y += sy;
+    if (x >= Lx) {
+      x -= Lx;
+      y += 1;
     }
   }
 }
