@@ -584,9 +584,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
 // rows exist once per SM; kNpt nodes per lane, kThreads threads, a multiple of 128 so
 // that the four sub-partitions of an SM hold equally many warps.  Few warps with room
 // for all their registers beat more warps that spill (measured on the 16384^2 D2Q5
-// lattice: 8 nodes per lane, 12 warps at up to 168 registers each, 153 G node
-// updates/s; 4 nodes per lane, 20 warps at up to 96 registers, 138; 24 warps at 80,
-// 133).
+// lattice: 8 nodes per lane, 12 warps at up to 168 registers each, 158 G node
+// updates/s; 8 nodes per lane in 16 warps at 128 registers (spills), 153; 4 nodes per
+// lane, 20 warps at up to 96 registers, 142).
 constexpr int kRows = 64;
 template <int SHAPE>
 struct WarpShape;
@@ -608,8 +608,8 @@ struct WarpShape<1> {
 // D2Q9 (nine planes, four Philox blocks and eleven draws per node): 4 nodes per lane
 // left in shared memory and collided two at a time (nine planes of vectors in
 // registers would cost 36 of them), 512 or 640 threads (measured on the 16384^2
-// lattice: 70.0 and 68.9 G node updates/s; with the vectors in registers, 512
-// threads: 62.9)
+// lattice: 72.6 and 68.9 G node updates/s; with the vectors in registers, 512
+// threads: 62.9 before the launch-wide Philox rounds were split off)
 template <int Q, int SHAPE>
 struct WarpShapeQ : WarpShape<SHAPE> {};
 template <>
