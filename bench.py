@@ -269,9 +269,7 @@ def measure_batched(torch, B, dev, rings=4096, T=5000, sample=64):
                 "ms_all_rings_estimated": plain_all_ms,
                 "sample": f"{len(idx)} rings evenly spaced in order of length, one context each, created and "
                           f"initialised before timing, {T} steps each (one launch per step) timed with CUDA events",
-                "identical_results": same,
-            "one_context": {"value": nu / (s_ms / 1e3) / 1e9, "unit": "GNUPS",
-                            "how": "the same bench steps in sequence through one context"}},
+                "identical_results": same},
             "speedup_vs_plain": plain_all_ms / ms, "autotune": tuning}
 
 
