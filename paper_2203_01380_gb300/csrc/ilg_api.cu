@@ -36,7 +36,7 @@ struct ilg_ctx {
   double* d_res = nullptr;
   uint32_t mode_cap = 0;
   uint32_t tb_depth = 0;                   // temporal blocking: steps per launch (0: off)
-  uint32_t general = 0;                    // high occupation: general collision path at once
+  uint32_t general = 0;                    // too many nodes would fail the fast collision: general at once
   int kernel_choice = -1;                  // single-step kernel chosen by ilg_autotune (-1: default)
   double omega_star = 0;
   unsigned long long* h_word = nullptr;    // pinned 8-byte readback
@@ -293,7 +293,7 @@ ilg_status ilg_init(ilg_ctx* c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   c->t = 0;
   c->has_state = true;
-  c->general = general_path(c->Q, c->omega_star, c->p.n0);
+  c->general = general_path(c->p.lattice, c->p.theta, c->omega_star, c->p.n0);
   return ILG_OK;
 }
 
@@ -306,7 +306,7 @@ static ilg_status update_path_choice(ilg_ctx* c) {
   ILG_CUDA(c, cudaMemcpyAsync(c->h_word, c->d_mass, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
            "read mass");
   ILG_CUDA(c, cudaStreamSynchronize(c->stream), "read mass");
-  c->general = general_path(c->Q, c->omega_star, double(*c->h_word) / (double(c->nodes) * c->Q));
+  c->general = general_path(c->p.lattice, c->p.theta, c->omega_star, double(*c->h_word) / (double(c->nodes) * c->Q));
   return ILG_OK;
 }
 

@@ -151,7 +151,7 @@ ilg_status ilg_batch_create(const ilg_params* params, uint32_t n, void* stream, 
     d.replica = q.replica;
     d.t = 0;
     d.particle = q.sampler == ILG_SAMPLER_PARTICLE ? 1u : 0u;
-    d.general = general_path(3, omega_star, q.n0) | d.particle;
+    d.general = general_path(ILG_D1Q3, q.theta, omega_star, q.n0, q.Lx) | d.particle;
     d.state_off = b->total;
     b->total += 3 * size_t(q.Lx);
     b->Lmax = std::max(b->Lmax, q.Lx);
@@ -247,7 +247,7 @@ ilg_status ilg_batch_set_state(ilg_batch* b, uint32_t i, const uint16_t* host, s
   uint64_t mass = 0;
   for (size_t k = 0; k < n; ++k) mass += host[k];
   const double om = b->p[i].omega_eff > 1.0 ? 2.0 - b->p[i].omega_eff : b->p[i].omega_eff;
-  b->desc[i].general = general_path(3, om, double(mass) / double(n)) | b->desc[i].particle;
+  b->desc[i].general = general_path(ILG_D1Q3, b->p[i].theta, om, double(mass) / double(n), b->p[i].Lx) | b->desc[i].particle;
   BCUDA(b, cudaMemcpyAsync(b->d_state + b->desc[i].state_off, host, sizeof(uint16_t) * n, cudaMemcpyHostToDevice, b->stream),
         "copy state in");
   BCUDA(b, cudaMemcpyAsync(b->d_desc + i, &b->desc[i], sizeof(ReplicaDesc), cudaMemcpyHostToDevice, b->stream), "copy desc");

@@ -44,7 +44,11 @@ void build_binomial_table(uint64_t P, uint32_t* T);
 void build_alias_table(uint64_t P, AliasEntry* out);
 uint32_t build_poisson_table(double lambda, uint32_t* T, uint32_t cap);
 uint64_t quantise_probability(double p);
-uint32_t general_path(int Q, double omega_star, double mean_occupation);
+// 1 when a lattice of this velocity set, theta, omega* and mean occupation per velocity
+// should skip the fast collision (too many of its nodes would fail it); sync_nodes: the
+// nodes that wait for one another every step (a warp's 32, or a batched ring's length)
+uint32_t general_path(int lattice, double theta, double omega_star, double mean_occupation,
+                      uint32_t sync_nodes = 32);
 void build_particle_bounds(int Q, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis, uint64_t* B);
 // table block of a lattice (kBlockWords words, kBlockWords9 for D2Q9)
 void build_table_block(int Q, uint32_t sampler, uint64_t P_omega, uint64_t P_rest, uint64_t P_axis,

@@ -207,7 +207,7 @@ bool admit(ilg_server* s, const Request& rq, Resident* out, cudaError_t* cerr, s
   const uint64_t Po = quantise_probability(omega_star), Pr = quantise_probability(w[0]);
   r.flip = rq.p.omega_eff > 1.0 ? 1u : 0u;
   r.particle = rq.p.sampler == ILG_SAMPLER_PARTICLE ? 1u : 0u;
-  r.general = general_path(5, omega_star, rq.p.n0) | r.particle;
+  r.general = general_path(ILG_D2Q5, rq.p.theta, omega_star, rq.p.n0) | r.particle;
   r.omega_mode = mode_of(Po);
   r.rest_mode = mode_of(Pr);
   std::vector<uint32_t> tables(kBlockWords, 0u);

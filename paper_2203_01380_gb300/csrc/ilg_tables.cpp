@@ -170,8 +170,44 @@ double axis_share(double theta) {
   return (4.0 * w[1]) / (1.0 - w[0]);
 }
 
-uint32_t general_path(int Q, double omega_star, double mean_occupation) {
-  return omega_star * Q * mean_occupation > 40.0 ? 1u : 0u;
+namespace {
+// P(X >= k) for X ~ Poisson(lambda); 1 where the terms would underflow (lambda that
+// large fails the fast collision anyway)
+double poisson_tail(double lambda, int k) {
+  if (lambda <= 0.0) return 0.0;
+  if (lambda > 700.0) return 1.0;
+  double term = std::exp(-lambda), below = 0.0;
+  for (int j = 0; j < k; ++j) {
+    below += term;
+    term *= lambda / double(j + 1);
+  }
+  return below >= 1.0 ? 0.0 : 1.0 - below;
+}
+}  // namespace
+
+// The fast collision needs every occupation below 64, at most 63 removed and at most 32
+// moving particles (D2Q9: 32 axis and 32 diagonal).  With Poisson occupations of the
+// given mean, removals and movers are thinned Poisson counts; the lattice goes straight
+// to the general collision when the expected share of nodes that fail the fast one is
+// above kGeneralShare, or, where sync_nodes nodes wait for one another every step (a
+// batched ring and its block barrier), when one of them is expected to fail in more
+// than about one step in three: trying the fast collision first then costs more than it
+// saves, since the warp or block that holds a failing node runs both collisions.
+uint32_t general_path(int lattice, double theta, double omega_star, double mean_occupation, uint32_t sync_nodes) {
+  constexpr double kGeneralShare = 0.02;
+  const double share = std::min(kGeneralShare, 0.3 / double(std::max<uint32_t>(sync_nodes, 1)));
+  double w[9];
+  weights(lattice, theta, w);
+  const int Q = lattice == ILG_D1Q3 ? 3 : (lattice == ILG_D2Q9 ? 9 : 5);
+  const double removed = omega_star * Q * mean_occupation, moving = removed * (1.0 - w[0]);
+  double fail = Q * poisson_tail(mean_occupation, 64) + poisson_tail(removed, 64);
+  if (lattice == ILG_D2Q9) {
+    const double a = axis_share(theta);
+    fail += poisson_tail(moving * a, 33) + poisson_tail(moving * (1.0 - a), 33);
+  } else {
+    fail += poisson_tail(moving, 33);
+  }
+  return fail > share ? 1u : 0u;
 }
 
 uint64_t quantise_probability(double p) {
