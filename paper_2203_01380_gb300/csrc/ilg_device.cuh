@@ -143,6 +143,26 @@ __device__ __forceinline__ void step_blocks(const StepKeys<NB>& k, const uint32_
   }
 }
 
+// A node's eight slot words (two blocks): from its launch's StepKeys where the caller
+// made them, else from the full rounds.
+__device__ __forceinline__ void slot_words8(const StepArgs& a, const StepKeys<2>* keys, uint32_t node, uint32_t t,
+                                            uint32_t (&W)[8]) {
+  if (keys) {
+    step_blocks<2>(*keys, a.rk, node, W);
+  } else {
+    const uint4 b0 = philox_rk(counter(node, t, a.replica, kDevTagStep | 0u), a.rk);
+    const uint4 b1 = philox_rk(counter(node, t, a.replica, kDevTagStep | 1u), a.rk);
+    W[0] = b0.x;
+    W[1] = b0.y;
+    W[2] = b0.z;
+    W[3] = b0.w;
+    W[4] = b1.x;
+    W[5] = b1.y;
+    W[6] = b1.z;
+    W[7] = b1.w;
+  }
+}
+
 __device__ __forceinline__ uint32_t lane_of(const uint4& b, uint32_t i) {
   return i == 0 ? b.x : (i == 1 ? b.y : (i == 2 ? b.z : b.w));
 }
@@ -296,7 +316,8 @@ __device__ __forceinline__ void collide(const StepArgs& a, const uint32_t* s, ui
 // probability of 0 or 2^32 draws nothing.
 template <int Q, int K, int S, class Tab = Alias8, bool OOL = false>
 __device__ __forceinline__ void collide_buffered(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
-                                                 const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
+                                                 const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb,
+                                                 const StepKeys<2>* keys = nullptr) {
   static_assert(K % 4 == 0, "whole Philox blocks");
   const Tab to = Tab::of(s, 0);
   const Tab tr = Tab::of(s, 1);
@@ -304,9 +325,8 @@ __device__ __forceinline__ void collide_buffered(const StepArgs& a, const uint32
   uint32_t need = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) need += extra(a.omega_mode, m[i]);
-  const uint4 b0 = philox_rk(counter(node, t, a.replica, kDevTagStep | 0u), a.rk);
-  const uint4 b1 = philox_rk(counter(node, t, a.replica, kDevTagStep | 1u), a.rk);
-  const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  uint32_t W[8];
+  slot_words8(a, keys, node, t, W);
   uint32_t filled = 0;
   auto gen = [&](uint32_t upto) {
     upto = upto < uint32_t(K) ? upto : uint32_t(K);
@@ -438,9 +458,10 @@ __device__ void collide_particle(const StepArgs& a, const uint32_t* s, uint32_t 
 // The general collision in whichever sampler the lattice uses.
 template <int Q, int K, int S, class Tab = Alias8, bool OOL = false>
 __device__ __forceinline__ void collide_general(const StepArgs& a, const uint32_t* s, uint32_t node, uint32_t t,
-                                                const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb) {
+                                                const uint32_t (&m)[Q], uint32_t (&out)[Q], uint32_t* xb,
+                                                const StepKeys<2>* keys = nullptr) {
   if (a.particle) collide_particle<Q>(a, s, node, t, m, out);
-  else collide_buffered<Q, K, S, Tab, OOL>(a, s, node, t, m, out, xb);
+  else collide_buffered<Q, K, S, Tab, OOL>(a, s, node, t, m, out, xb, keys);
 }
 
 // The collision of one node, fast path: every occupation <= 63, at most 63
@@ -451,7 +472,8 @@ __device__ __forceinline__ void collide_general(const StepArgs& a, const uint32_
 // exceed 65535 here (mass is conserved and at most 5 * 63).
 template <int Q, class Tab = Alias8>
 __device__ __forceinline__ bool collide_try_fast(const StepArgs& a, const uint32_t* s, uint32_t node,
-                                                 uint32_t t, const uint32_t (&m)[Q], uint32_t (&out)[Q]) {
+                                                 uint32_t t, const uint32_t (&m)[Q], uint32_t (&out)[Q],
+                                                 const StepKeys<2>* keys = nullptr) {
   const Tab to = Tab::of(s, 0);
   const Tab tr = Tab::of(s, 1);
   if (a.omega_mode != kTable || a.rest_mode != kTable) return false;
@@ -459,10 +481,9 @@ __device__ __forceinline__ bool collide_try_fast(const StepArgs& a, const uint32
 #pragma unroll
   for (int i = 1; i < Q; ++i) any |= m[i];
   if (any >> 6) return false;
-  const uint4 b0 = philox_rk(counter(node, t, a.replica, kDevTagStep | 0u), a.rk);
-  const uint4 b1 = philox_rk(counter(node, t, a.replica, kDevTagStep | 1u), a.rk);
   // slot words: thinning 0..Q-1, rest Q, moving Q+1 (and Q+2)
-  const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  uint32_t W[8];
+  slot_words8(a, keys, node, t, W);
   uint32_t r[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) r[i] = to(m[i], W[i]);

@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(St
   const uint32_t stride_y = stride / a.Lx, stride_x = stride - stride_y * a.Lx;
   uint32_t node = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t y = node / a.Lx, x = node - y * a.Lx;
+  const StepKeys<2> keys = step_keys<2>(a, t);  // the launch-wide Philox rounds of the slot blocks
   for (; node < nodes; node += stride) {
     uint32_t n[Q], m[Q], post[Q];
 #pragma unroll
@@ -69,8 +70,8 @@ __global__ void __launch_bounds__(kStepThreads, kStepBlocksPerSm) step_kernel(St
       m[3] = a.flip ? n[4] : n[3];
       m[4] = a.flip ? n[3] : n[4];
     }
-    if (a.general || !collide_try_fast<Q, StepTab>(a, s, node, t, m, post)) {
-      collide_general<Q, kExtWords, kStepThreads, StepTab, true>(a, s, node, t, m, post, xb);
+    if (a.general || !collide_try_fast<Q, StepTab>(a, s, node, t, m, post, &keys)) {
+      collide_general<Q, kExtWords, kStepThreads, StepTab, true>(a, s, node, t, m, post, xb, &keys);
 #pragma unroll
       for (int i = 0; i < Q; ++i) bad |= post[i] > 65535u;
     }
