@@ -189,7 +189,7 @@ KERNEL_NAMES = {"vec8": "step_vec_kernel<5, 8>", "vec4": "step_vec_kernel<5, 4>"
 
 
 def hbm_roofline(nodes, launch_ms, choice):
-    """Sec. 8(d)'s roofline of the dominant kernel: every occupation read and written
+    """The HBM roofline of the dominant kernel: every occupation read and written
     once (20 B per D2Q5 node update) per launch, against the measured copy bandwidth."""
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
@@ -500,6 +500,30 @@ def measure_d2q9(torch, B, dev, side):
             "identical_results": bool(all(x == obs[0] for x in obs))}
 
 
+def measure_e2e_one_context(torch, lat, args, modes, stream, dev, world, nu, barrier):
+    """The e2e metric through one context: every bench step copies its state in from and
+    out to pinned host memory around its steps and observables, one after another."""
+    host = torch.empty(lat.size, dtype=torch.uint16, pin_memory=True).numpy()
+    lat.get_state(host.reshape(lat.shape))
+    res = torch.empty(lat.size, dtype=torch.uint16, pin_memory=True).numpy()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lat.set_state(host, 0)
+        lat.step(args.tsteps)
+        lat.observables(modes)
+        lat.get_state(res.reshape(lat.shape))
+    e1.record(stream)
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    return {"value": nu / (ms / 1e3) / 1e9, "unit": "GNUPS",
+            "h2d_bytes_per_step": int(lat.size * 2 + 8 * len(modes)),
+            "d2h_bytes_per_step": int(lat.size * 2 + 8 + 32 * len(modes)),
+            "how": "one context: each bench step's state copied in from and out to pinned host memory "
+                   "through ilg_set_state / ilg_get_state around its steps"}
+
+
 def measure_e2e(torch, B, lat, cfg, args, modes, stream, dev, world, nu, barrier):
     """The metric end to end through the C ABI with host buffers: every bench step
     copies its initial state in from pinned host memory (ilg_set_state), takes its
@@ -779,7 +803,13 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(torch, B, lat, cfg, args, modes, stream, dev, world, nu, barrier)
+        try:
+            e2e = measure_e2e(torch, B, lat, cfg, args, modes, stream, dev, world, nu, barrier)
+        except (RuntimeError, MemoryError, B.IlgError) as ex:
+            # a second context or three pinned state buffers did not fit: one context alone
+            torch.cuda.synchronize(dev)
+            e2e = measure_e2e_one_context(torch, lat, args, modes, stream, dev, world, nu, barrier)
+            e2e["pipelined_unavailable"] = str(ex).splitlines()[0][:200]
 
     alu = alu_roofline(B, nodes, launch_ms, stream) if rank == 0 else None
 
