@@ -195,6 +195,36 @@ def test_overflow_rolls_back(B):
     assert np.array_equal(got, cur)
 
 
+@pytest.mark.parametrize("kernel", [6, 7])
+@pytest.mark.parametrize("lattice,Lx,Ly", [(1, 4096, 1), (2, 256, 64), (3, 256, 32)])
+def test_overflow_in_staged_warp_step(B, kernel, lattice, Lx, Ly):
+    """A node holding 65535 particles in every velocity overflows through the staged
+    warp step (its general collision: the fast one refuses the node) on a lattice whose
+    mean stays low enough for that kernel; the context reports the overflow and holds
+    the state of the step that failed, as the oracle names it."""
+    Q = {1: 3, 2: 5, 3: 9}[lattice]
+    s = inputs.random_state(Q, Ly, Lx, 3.0, seed=Lx + Q)
+    s[:, Ly // 2, 37] = 65535
+    cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, omega_eff=1.9, seed=5)
+    ref = O.Lattice(**cfg)
+    cur, fail_t = s.copy(), None
+    for t in range(6):
+        try:
+            cur = ref.step(cur, t)
+        except OverflowError:
+            fail_t = t
+            break
+    assert fail_t is not None
+    with B.Lattice(**cfg) as lat:
+        lat.set_step_kernel(kernel)
+        lat.set_state(s, 0)
+        with pytest.raises(B.IlgError) as e:
+            lat.step(6)
+        assert e.value.status == B.ILG_E_OVERFLOW
+        got, t = lat.get_state()
+    assert t == fail_t and np.array_equal(got, cur)
+
+
 def test_invalid_arguments(B):
     bad = [dict(lattice=3, Lx=10), dict(lattice=1, Lx=2), dict(lattice=2, Lx=10, Ly=2),
            dict(lattice=1, Lx=10, omega_eff=0.0), dict(lattice=1, Lx=10, omega_eff=2.5),
