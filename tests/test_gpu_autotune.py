@@ -16,19 +16,22 @@ def B():
     return binding
 
 
+@pytest.mark.parametrize("omega", [1.7, 0.6])
 @pytest.mark.parametrize("kernel", [0, 1, 2, 5, 6, 7, -1])
 @pytest.mark.parametrize("lattice,Lx,Ly,mean,hot", [(2, 96, 40, 10.0, 3), (2, 100, 23, 8.0, 0), (1, 2052, 1, 20.0, 2),
                                                     (2, 2056, 9, 6.0, 0), (2, 8200, 3, 6.0, 1),
                                                     (1, 16392, 1, 20.0, 2)])
-def test_every_shape_is_bit_exact(B, kernel, lattice, Lx, Ly, mean, hot):
+def test_every_shape_is_bit_exact(B, kernel, lattice, Lx, Ly, mean, hot, omega):
     """8- and 4-node vectors in row tiles, 8-node vectors in warp segments (rows of 96,
     100, 2052, 2056 nodes: several tiles, ragged tails, occupations that need the
     general pass; rows of 8200 and 16392 nodes: segments of 8192 nodes and a one-vector
     remainder), 4-node vectors in warp segments (the row split into segments whose
-    end values are stored by the warp that owns them), node-parallel, default."""
+    end values are stored by the warp that owns them), node-parallel, default; with
+    the flip (omega_eff 1.7) and without it (0.6: the kernels' other compile-time
+    plane order)."""
     Q = 3 if lattice == 1 else 5
     s0 = inputs.random_state(Q, Ly, Lx, mean, seed=Lx + Ly, hot=hot, hot_value=500)
-    cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, omega_eff=1.7, seed=9, replica=1)
+    cfg = dict(lattice=lattice, Lx=Lx, Ly=Ly, omega_eff=omega, seed=9, replica=1)
     with B.Lattice(**cfg) as lat:
         lat.set_step_kernel(kernel)
         lat.set_state(s0, 3)
