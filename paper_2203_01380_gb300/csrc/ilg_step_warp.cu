@@ -198,7 +198,10 @@ __device__ __noinline__ bool slow_nodes(const StepArgs& a, const uint32_t* gt, u
 
 // Flip and collide the NPT nodes of one vector (first node `node0`) into the packed
 // post-collision planes P.  N holds the vector's occupations with the flip already
-// applied (plane i loaded from the flipped source).
+// applied (plane i loaded from the flipped source); slot is where they came from in
+// the tile buffer and scratch the lane's slot for the general collision's results
+// (both read only by the out-of-line general collision); keys: the launch-wide part
+// of every node's slot blocks.
 template <int Q, int ROWS, int NPT>
 __device__ __forceinline__ void collide_vec(const StepArgs& a, const StepKeys<Q == 9 ? 4 : 2>& keys, const uint2* to,
                                             const uint2* tr, const uint2* ta, uint32_t node0, uint32_t t,
