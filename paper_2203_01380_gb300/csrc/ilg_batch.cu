@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
     uint64_t mass = 0;
     const bool rec = b.record != nullptr;
     const uint32_t mrec = rec ? uint32_t(((int64_t(b.record_mode) % int64_t(L)) + L) % L) : 0u;
+    const longlong2* trig = b.trig ? b.trig + d.state_off / 3 : nullptr;  // this ring's values
     if (rec) {
       unsigned long long part = 0;
       for (uint32_t x = tid; x < L; x += THREADS)
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
       __syncthreads();
       mass = s_mass;
       // partials of state 0 into slot 0 (finalised after the first step's barrier)
-      ring_partials<THREADS>(buf0, L, b.Lmax, mass, mrec, b.trig, s_red[0]);
+      ring_partials<THREADS>(buf0, L, b.Lmax, mass, mrec, trig, s_red[0]);
     }
 
     uint16_t* src = buf0;
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) batch_d1q3_kernel(Bat
         // state s was reduced into slot s & 1 before this step's barrier: finalise
         // it; then the warps reduce the new state s + 1 into the other slot
         if (tid == 0) ring_finalise<THREADS>(s_red[s & 1], b.record + (size_t(r) * (b.T + 1) + s) * 4);
-        ring_partials<THREADS>(src, L, b.Lmax, mass, mrec, b.trig, s_red[(s + 1) & 1]);
+        ring_partials<THREADS>(src, L, b.Lmax, mass, mrec, trig, s_red[(s + 1) & 1]);
       }
     }
     if (rec && s_fail < 0) {
@@ -368,10 +369,16 @@ __global__ void __launch_bounds__(256) batch_obs_kernel(const ReplicaDesc* __res
   }
 }
 
-// trig[x] = fixed-point (cos, sin) of 2 pi ((m x) mod L) / L, x = 0..L-1.
-__global__ void batch_trig_kernel(uint32_t L, uint32_t m, longlong2* __restrict__ trig) {
-  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < L; x += gridDim.x * blockDim.x)
-    trig[x] = trig_fixed(uint32_t((uint64_t(m) * x) % L), L);
+// ring r's trig[state_off_r / 3 + x] = fixed-point (cos, sin) of 2 pi ((m_r x) mod L_r) / L_r,
+// m_r the mode reduced modulo L_r: the values ring_partials would compute per node
+__global__ void batch_trig_rings_kernel(const ReplicaDesc* __restrict__ desc, uint32_t n, int32_t mode,
+                                        longlong2* __restrict__ trig) {
+  for (uint32_t r = blockIdx.x; r < n; r += gridDim.x) {
+    const uint32_t L = desc[r].L;
+    const uint32_t m = uint32_t(((int64_t(mode) % int64_t(L)) + L) % L);
+    longlong2* out = trig + desc[r].state_off / 3;
+    for (uint32_t x = threadIdx.x; x < L; x += blockDim.x) out[x] = trig_fixed(uint32_t((uint64_t(m) * x) % L), L);
+  }
 }
 
 // Raw 128-bit sums (L 2^62 re, L 2^62 im) -> (re, im) in double, rounded once and
@@ -479,9 +486,8 @@ cudaError_t launch_batch_convert(const ReplicaDesc* desc, const long long* raw, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_trig(uint32_t L, int32_t mode, longlong2* trig, cudaStream_t s) {
-  const uint32_t m = uint32_t(((int64_t(mode) % int64_t(L)) + L) % L);
-  batch_trig_kernel<<<(L + 255) / 256, 256, 0, s>>>(L, m, trig);
+cudaError_t launch_batch_trig_rings(const ReplicaDesc* desc, uint32_t n, int32_t mode, longlong2* trig, cudaStream_t s) {
+  batch_trig_rings_kernel<<<n < 1024u ? n : 1024u, 256, 0, s>>>(desc, n, mode, trig);
   return cudaGetLastError();
 }
 

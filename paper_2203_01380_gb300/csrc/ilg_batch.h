@@ -41,8 +41,9 @@ struct BatchArgs {
   long long* record;       // n x (T + 1) x 4: exact sums (L 2^62 re, L 2^62 im) as 128-bit
                            // (lo, hi) pairs of the recorded mode at the launch's start, then
                            // after every step; or NULL
-  const longlong2* trig;   // fixed-point (cos, sin) of the recorded mode indexed by x when
-                           // every ring has one length, else NULL (computed per node)
+  const longlong2* trig;   // fixed-point (cos, sin) of the recorded mode, ring r's values at
+                           // x + state_off / 3 (its nodes' place in the batch); or NULL
+                           // (computed per node and step)
   uint16_t* states;        // state of every ring after every step, or NULL: ring r's
                            // T x 3 L_r occupations at T * state_off, step s at s * 3 L_r
 };
@@ -60,7 +61,9 @@ cudaError_t launch_batch_amp(const ReplicaDesc* desc, const double* record, uint
                              cudaStream_t s);
 cudaError_t launch_batch_convert(const ReplicaDesc* desc, const long long* raw, uint32_t n, uint32_t T, double* rec,
                                  cudaStream_t s);
-cudaError_t launch_batch_trig(uint32_t L, int32_t mode, longlong2* trig, cudaStream_t s);
+// every ring's table of the recorded mode at its nodes' place in the batch (desc on the
+// device, n rings)
+cudaError_t launch_batch_trig_rings(const ReplicaDesc* desc, uint32_t n, int32_t mode, longlong2* trig, cudaStream_t s);
 cudaError_t launch_batch_ensemble(const double* record, uint32_t n, uint32_t T, double* out, cudaStream_t s);
 
 }  // namespace ilg

@@ -40,8 +40,8 @@ struct ilg_batch {
   size_t out_cap = 0;
   uint16_t* d_states = nullptr;       // per-step states (ilg_batch_run_record), T x total
   size_t states_cap = 0;
-  longlong2* d_trig = nullptr;        // fixed-point trigonometric table of the ensemble mode
-  uint32_t trig_cap = 0;
+  longlong2* d_trig = nullptr;        // fixed-point trigonometric table of the recorded mode
+  size_t trig_cap = 0;                 // entries (one per node of the batch)
   unsigned long long* d_mass = nullptr;
   double* d_amp = nullptr;
   StepArgs common{};
@@ -288,20 +288,22 @@ ilg_status batch_launch(ilg_batch* b, uint32_t T, int32_t record_mode, bool rec,
     }
   }
   if (trig) {
-    // every ring has length desc[0].L: one table indexed by x, rebuilt each call
-    const uint32_t L = b->desc[0].L;
-    if (b->trig_cap < L) {
+    // every ring's values of the recorded mode at its nodes' place, rebuilt each call
+    // (the fixed-point cos and sin take double-precision sincospi: once per node here
+    // instead of once per node and step in the kernel)
+    const size_t nodes = b->total / 3;
+    if (b->trig_cap < nodes) {
       cudaFree(b->d_trig);
       b->d_trig = nullptr;
       b->trig_cap = 0;
-      BCUDA(b, dev_alloc(&b->d_trig, sizeof(longlong2) * L), "cudaMalloc trig");
-      b->trig_cap = L;
+      BCUDA(b, dev_alloc(&b->d_trig, sizeof(longlong2) * nodes), "cudaMalloc trig");
+      b->trig_cap = nodes;
       if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
       }
     }
-    BCUDA(b, launch_batch_trig(L, record_mode, b->d_trig, b->stream), "trig table");
+    BCUDA(b, launch_batch_trig_rings(b->d_desc, b->n, record_mode, b->d_trig, b->stream), "trig table");
   }
   if (states && b->states_cap < size_t(T) * b->total) {
     cudaFree(b->d_states);
@@ -401,7 +403,7 @@ ilg_status ilg_batch_run_record(ilg_batch* b, uint32_t T, int32_t record_mode, d
     if (st == ILG_OK) st = ensure_doubles(b, &b->d_rec, &b->rec_cap, size_t(b->n) * (size_t(T) + 1) * 2);
     if (st != ILG_OK) return st;
   }
-  ilg_status st = batch_launch(b, T, record_mode, rec, false, failed, states);
+  ilg_status st = batch_launch(b, T, record_mode, rec, rec, failed, states);
   if (st != ILG_OK) return st;
   if (rec) {
     BCUDA(b, launch_batch_convert(b->d_desc, b->d_record, b->n, T, b->d_rec, b->stream), "convert record");
