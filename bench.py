@@ -531,7 +531,6 @@ def measure_e2e(torch, B, lat, cfg, args, modes, stream, dev, world, nu, barrier
     contexts on two streams, each driven by its own host thread, take alternate bench
     steps, so one step's copies overlap the other's kernels (each result is the one a
     single context gives: the same input, the same counter-keyed random numbers)."""
-    import threading
     st2 = torch.cuda.Stream(dev)
     lat2 = B.Lattice(**cfg, stream=st2)
     if args.kernel:
